@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""GStencil/s of the GB300 stencil engine on the Box-2D3R FP64 16384^2 workload.
+
+One bench step = one call of stencil_run over the whole workload (100 steps
+of Box-2D3R FP64 on a 16384 x 16384 interior with a fixed zero halo of width
+3), i.e. every fused sweep of the dispatched plan plus the halo copy.  The
+plan (path and fusion depth t) is what the library's model-based dispatcher
+picks; `--t` / `--path` force one.  Inputs are seeded synthetic data of the
+paper's kind (weights U(0,1) normalised to sum 1, field U[0,1)).
+
+Printed: one JSON line (rank 0).  value = point-updates per second / 1e9
+summed over ranks (each rank runs its own replica: weak scaling), timed with
+CUDA events between barriers, inputs resident in HBM and larger than L2.
+e2e = the same metric through stencil_run_host (pinned host buffers, copies
+inside the timed region).  roofline = the dominant kernel (the sweep)
+against the FP64 FMA pipe (ALU-bound) or HBM (memory-bound configurations).
+cpu_baseline = the CPU oracle on a bounded sample of the same workload.
+
+--impl reference times the CPU oracle alone (the comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GStencil/s and % of roofline, mixed-precision & batched vs plain FP64, 1 GB300"
+UNIT = "GStencil/s"
+
+WORKLOADS = {
+    # name: shape, d, r, interior dims, steps per run, dtype, seed
+    "box2d3r_f64_16384": dict(shape="box", d=2, r=3, dims=(16384, 16384), steps=100, dtype="f64", seed=2),
+    "star2d1r_f64_512": dict(shape="star", d=2, r=1, dims=(512, 512), steps=10, dtype="f64", seed=1),
+    "star3d2r_f64_512": dict(shape="star", d=3, r=2, dims=(512, 512, 512), steps=50, dtype="f64", seed=3),
+    "star3d2r_f32_512": dict(shape="star", d=3, r=2, dims=(512, 512, 512), steps=50, dtype="f32", seed=3),
+    "box3d1r_f64_512": dict(shape="box", d=3, r=1, dims=(512, 512, 512), steps=50, dtype="f64", seed=3),
+    "box3d1r_f32_512": dict(shape="box", d=3, r=1, dims=(512, 512, 512), steps=50, dtype="f32", seed=3),
+    "box2d2r_f32_16384": dict(shape="box", d=2, r=2, dims=(16384, 16384), steps=1000, dtype="f32", seed=4,
+                              field="sine"),
+}
+DEFAULT = "box2d3r_f64_16384"
+
+# Derived ALU peaks (152 SMs x 2070 MHz maximum clock; per SM and clock: 2 FP64
+# FMA lanes = 4 FLOP, 128 FP32 FMA lanes = 256 FLOP).
+SMS, SM_MAX_MHZ = 152, 2070.0
+ALU_PEAK_TFLOPS = {"f64": SMS * SM_MAX_MHZ * 1e6 * 4 / 1e12, "f32": SMS * SM_MAX_MHZ * 1e6 * 256 / 1e12}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def points_of(cfg):
+    return math.prod(cfg["dims"])
+
+
+def config_json(name, cfg, extra=None):
+    c = {"workload": f"{cfg['shape'].capitalize()}-{cfg['d']}D{cfg['r']}R {cfg['dtype'].upper()} "
+                     f"{'x'.join(str(n) for n in cfg['dims'])}, {cfg['steps']} steps",
+         "name": name, "shape": cfg["shape"], "d": cfg["d"], "r": cfg["r"],
+         "dims": list(cfg["dims"]), "steps_per_run": cfg["steps"], "halo": "fixed zeros, width r",
+         "l2": "inputs larger than L2 (no flush)" if points_of(cfg) * (8 if cfg["dtype"] == "f64" else 4) > 129e6
+         else "inputs smaller than L2"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return None
+        self.file.flush()
+        with open(self.file.name) as f:
+            rows = [[c.strip() for c in line.split(",")] for line in f if line.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_baseline(cfg, budget_s=15.0):
+    """The oracle (as it stands) on a bounded sample of the workload: the same
+    stencil and dtype on a smaller grid, steps chosen for ~budget_s of CPU time."""
+    import numpy as np
+
+    import oracle
+    from paper_2603_00477_gb300 import inputs
+    d = cfg["d"]
+    side = 1024 if d == 2 else 96
+    dims = (side,) * d
+    npdt = np.float64 if cfg["dtype"] == "f64" else np.float32
+    w, u = inputs.problem(cfg["shape"], d, cfg["r"], dims, seed=cfg["seed"], dtype=npdt)
+    u = u.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(cfg["steps"], int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, steps)
+    el = time.perf_counter() - t0
+    return {"value": math.prod(dims) * steps / el / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{cfg['shape']}-{d}D{cfg['r']}R {cfg['dtype']} on a {'x'.join(map(str, dims))} interior, "
+                      f"{steps} steps, FP64 C oracle with OpenMP ({el:.1f} s)"}
+
+
+def run_reference(args, cfg, name, rank):
+    """Comparison arm: the CPU oracle on the machine's host cores."""
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_2603_00477_gb300 import inputs
+    oracle.build()
+    d = cfg["d"]
+    side = 1024 if d == 2 else 96
+    dims = (side,) * d
+    npdt = np.float64 if cfg["dtype"] == "f64" else np.float32
+    w, u = inputs.problem(cfg["shape"], d, cfg["r"], dims, seed=cfg["seed"], dtype=npdt)
+    u = u.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, 1)
+    one = time.perf_counter() - t0
+    per_step_budget = min(8.0, 150.0 / max(1, args.steps + args.warmup))
+    sample_steps = max(1, min(cfg["steps"], int(per_step_budget / max(one, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, sample_steps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, sample_steps)
+    el = time.perf_counter() - t0
+    value = math.prod(dims) * sample_steps * args.steps / el / 1e9
+    sample = (f"{cfg['shape']}-{d}D{cfg['r']}R {cfg['dtype']} on a {'x'.join(map(str, dims))} interior, "
+              f"{sample_steps} steps per bench step, FP64 C oracle with OpenMP")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded splitmix64)",
+            "config": config_json(name, cfg, {"sample": sample}), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu summary, if
+    the kernel source has not changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kernel_key)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for src in rec.get("sources", []):
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec.get("sources_sha256"):
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--t", type=int, default=0, help="force the fusion depth (0 = model)")
+    ap.add_argument("--path", default="auto")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-(path, t) sweep")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    cfg = WORKLOADS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg, args.config, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_00477_gb300 import binding as B
+    from paper_2603_00477_gb300 import build as gbuild
+    from paper_2603_00477_gb300 import inputs
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    gbuild.build()
+    B.load()
+    peaks, peaks_src = measured_peaks()
+    B.stencil_set_peaks(hbm_bytes_per_s=float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # cpu baseline first (no GPU work yet in this process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline(cfg)
+
+    npdt = np.float64 if cfg["dtype"] == "f64" else np.float32
+    w, u = inputs.problem(cfg["shape"], cfg["d"], cfg["r"], cfg["dims"], seed=cfg["seed"], dtype=npdt,
+                          field=cfg.get("field", "uniform"))
+    plan = B.Plan(cfg["shape"], cfg["d"], cfg["r"], w, cfg["dtype"], cfg["dims"], args.t)
+    if args.path != "auto":
+        plan.set_option("path", args.path)
+    if args.precision:
+        plan.set_option("precision", args.precision)
+    info = plan.info()
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    plan.ensure_workspace(x.device)
+    stream = torch.cuda.current_stream()
+    steps = cfg["steps"]
+    pts = points_of(cfg)
+
+    for _ in range(args.warmup):
+        plan.run(x, y, steps)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    with sampler:
+        n0 = B.stencil_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.run(x, y, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = B.stencil_launch_count() - n0
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.summary()
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * pts * steps * args.steps / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel (the sweep): algorithmic work per launch /
+    # average launch duration over the timed region
+    t = info["t"]
+    nsweeps = steps // t + (1 if steps % t else 0)
+    sweep_launches = nsweeps * args.steps
+    avg_launch_s = ms / 1e3 / sweep_launches
+    K = info["K"]
+    D = 8 if cfg["dtype"] == "f64" else 4
+    kernel = {1: "cu2d_sweep" if cfg["d"] == 2 else "cu3d_sweep"}.get(info["path"], "tc_sweep")
+    kernel_key = f"{kernel}:{args.config}:{info['path_name']}:t{t}"
+    traffic = traffic_record(kernel_key)
+    if info["memory_bound"]:
+        achieved = pts * 2 * D / avg_launch_s / 1e9  # one read + one write per point and sweep
+        peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": f"hbm_gbs of {peaks_src} peaks"}
+    else:
+        flops = pts * 2 * K * (steps / nsweeps)  # useful FLOP of one sweep (t steps; remainder averaged)
+        achieved = flops / avg_launch_s / 1e12
+        peak = ALU_PEAK_TFLOPS[cfg["dtype"]]
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"derived: 152 SMs x 2070 MHz x {'4' if D == 8 else '256'} FLOP/clk/SM "
+                               f"({cfg['dtype'].upper()} FMA pipe)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic
+    roof["kernel"] = kernel_key
+    roof["avg_launch_ms"] = avg_launch_s * 1e3
+    roof["launches_timed"] = sweep_launches
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(u).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        plan.run_host(h_in, h_out, steps)  # warm (workspace of three grids)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.run_host(h_in, h_out, steps)
+        el = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        nbytes = h_in.numel() * h_in.element_size()
+        e2e = {"value": world * pts * steps * args.steps / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "api": "stencil_run_host (pinned host buffers)"}
+        del h_in, h_out
+        plan._ws = None
+        torch.cuda.empty_cache()
+        plan.ensure_workspace(x.device)
+
+    # per-(path, t) sweep of the headline workload next to the model's prediction
+    sweep = None
+    if not args.no_sweep and rank == 0:
+        sweep = []
+        for path in ("cuda_core", "tensor_core"):
+            for tt_ in (1, 2, 3, 4):
+                try:
+                    p2 = B.Plan(cfg["shape"], cfg["d"], cfg["r"], w, cfg["dtype"], cfg["dims"], tt_)
+                    p2.set_option("path", path)
+                except B.StencilError:
+                    continue
+                p2._ws = plan._ws
+                B.stencil_plan_set_workspace(p2.handle, plan._ws.data_ptr(), plan._ws.numel())
+                p2.run(x, y, steps)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                p2.run(x, y, steps)
+                b.record(stream)
+                torch.cuda.synchronize()
+                i2 = p2.info()
+                sweep.append({"path": path, "t": tt_, "gstencils": pts * steps / (a.elapsed_time(b) / 1e3) / 1e9,
+                              "model_gstencils": i2["predicted_gstencils"], "alpha": i2["alpha"],
+                              "sparsity": i2["sparsity"]})
+                p2._ws = None
+                p2.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": cfg["dtype"],
+            "data": "synthetic (seeded splitmix64: weights U(0,1) normalised, field U[0,1))",
+            "config": config_json(args.config, cfg, {"parallelism": f"replicas x{world}",
+                                                     "path": info["path_name"], "t": t,
+                                                     "precision": info["precision_name"],
+                                                     "tile": info["tile"]}),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "model": {"predicted_gstencils": info["predicted_gstencils"], "scenario": info["scenario"],
+                      "intensity": info["intensity"], "ridge": info["ridge"],
+                      "memory_bound": bool(info["memory_bound"])},
+            "sweep": sweep}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

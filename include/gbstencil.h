@@ -1,0 +1,222 @@
+/*
+ * gbstencil.h -- C ABI of the GB300 (sm_103a) stencil engine.
+ *
+ * The engine runs repeated, temporally fused star/box stencil sweeps
+ * (dimensionality d in {2,3}, radius r, fusion depth t) on one GPU, on a
+ * CUDA-core path (temporal blocking in shared memory/registers) or a
+ * tensor-core path (the t-step composite stencil as banded Toeplitz MMA
+ * tiles), and picks the path and t with the performance model of
+ * arxiv 2603.00477 ("Do We Need Tensor Cores for Stencil Computations?").
+ *
+ * What one step computes (paper Sec. 1, the stencil definition): every
+ * interior point p of the grid becomes
+ *       u_{n+1}[p] = sum_{o in O} w_o * u_n[p + o],
+ * where O is the box [-r, r]^d or the star (offsets with at most one non-zero
+ * coordinate) and the halo cells keep their values (fixed Dirichlet
+ * boundary).  O is ordered lexicographically, first axis outermost, each
+ * coordinate ascending from -r, and the K weights follow that order
+ * (K = (2r+1)^d for a box, 2dr+1 for a star).  The result after `steps` steps
+ * does not depend on t or on the path beyond rounding.
+ *
+ * Grid layout (every buffer): row-major, last axis contiguous, stored
+ * extents dims[i] + 2r (the interior plus a halo of width r on every side);
+ * element type double (STENCIL_F64) or float (STENCIL_F32).
+ *
+ * Conventions for every call:
+ *   - No exception crosses this boundary; every call returns a status.
+ *   - Device pointers are CUDA device memory of the current device
+ *     (allocated by the caller, e.g. through PyTorch), never freed here.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Kernels are
+ *     launched on it and the call returns without synchronising; a CUDA
+ *     error reported at launch gives STENCIL_ERR_CUDA, and an asynchronous
+ *     fault surfaces as STENCIL_ERR_CUDA on a later call.
+ *   - A plan is not thread safe: use one plan per stream.
+ *   - stencil_last_error() returns a human-readable message for the last
+ *     failed call of the calling thread.
+ */
+#ifndef GBSTENCIL_H
+#define GBSTENCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *stencil_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    STENCIL_OK = 0,
+    STENCIL_ERR_INVALID_ARG = 1, /* a bad argument; nothing was launched */
+    STENCIL_ERR_UNSUPPORTED = 2, /* valid, but no kernel for this case   */
+    STENCIL_ERR_CUDA = 3,        /* a CUDA call or launch failed          */
+    STENCIL_ERR_OOM = 4,         /* workspace missing or too small        */
+    STENCIL_ERR_TIMEOUT = 5      /* a bounded device wait ran out         */
+} stencil_status;
+
+typedef enum { STENCIL_BOX = 0, STENCIL_STAR = 1 } stencil_shape;
+typedef enum { STENCIL_F64 = 0, STENCIL_F32 = 1 } stencil_dtype;
+
+/* Execution path.  CUDA_CORE: temporal fusion with intermediates kept on
+ * chip (paper Sec. 3.2.2).  TENSOR_CORE: kernel fusion into the composite
+ * stencil w^(t) run as dense MMA tiles (Sec. 2.2, 3.2.3).  SPARSE_TENSOR_CORE:
+ * the same on 2:4 structured-sparse MMA (Sec. 4.3). */
+typedef enum {
+    STENCIL_PATH_AUTO = 0,
+    STENCIL_PATH_CUDA_CORE = 1,
+    STENCIL_PATH_TENSOR_CORE = 2,
+    STENCIL_PATH_SPARSE_TENSOR_CORE = 3
+} stencil_path;
+
+/* Arithmetic of the products.  NATIVE: the grid's own type (FP64 grids:
+ * FP64 FMA or FP64 MMA; FP32 grids: FP32 FMA).  TF32: one TF32 product with
+ * FP32 accumulation.  TF32X3 / BF16X3: operands split into hi + lo parts,
+ * three products (hi*hi + hi*lo + lo*hi) accumulated in FP32.  ANY: the
+ * dispatcher may pick any form the grid type allows. */
+typedef enum {
+    STENCIL_PREC_NATIVE = 0,
+    STENCIL_PREC_TF32 = 1,
+    STENCIL_PREC_TF32X3 = 2,
+    STENCIL_PREC_BF16X3 = 3,
+    STENCIL_PREC_ANY = 4
+} stencil_precision;
+
+/* Peak rates the model uses (bytes/s and FLOP/s).  Table 1 of the paper:
+ * B (bandwidth) and P per unit.  Zero fields keep their current value. */
+typedef struct {
+    double hbm_bytes_per_s;  /* B                                   */
+    double cu_f64_flops;     /* P_CU, FP64 FMA pipe                 */
+    double cu_f32_flops;     /* P_CU, FP32 FMA pipe                 */
+    double tc_f64_flops;     /* P_TC, FP64 MMA                      */
+    double tc_tf32_flops;    /* P_TC, dense TF32 MMA                */
+    double tc_bf16_flops;    /* P_TC, dense BF16 MMA                */
+    double sptc_tf32_flops;  /* P_SpTC, 2:4 sparse TF32 (dense-equivalent) */
+    double sptc_bf16_flops;  /* P_SpTC, 2:4 sparse BF16 (dense-equivalent) */
+} stencil_peaks;
+
+/* What the plan decided and what the model predicts for it. */
+typedef struct {
+    int path;             /* stencil_path actually used                      */
+    int precision;        /* stencil_precision actually used                 */
+    int t;                /* fusion depth                                    */
+    int tile[3];          /* output tile per CTA, slowest axis first         */
+    int K;                /* points of the pattern                           */
+    int K_fused;          /* K^(t), points of the composite kernel           */
+    double alpha;         /* K^(t)/(tK)  (Eq. 9); 1 on the CUDA-core path    */
+    double sparsity;      /* S of the MMA tiles (useful/issued); 1 on CU     */
+    double beta;          /* products issued per useful product (1 or 3)     */
+    double intensity;     /* FLOP/byte of the chosen path (Eq. 8 / Eq. 12)   */
+    double ridge;         /* P/B of the unit that runs the path              */
+    int scenario;         /* 1..4 (Sec. 4.1) of CU vs TC at this t           */
+    int memory_bound;     /* 1 if the chosen path is below its ridge         */
+    double predicted_gstencils;    /* point-updates/s / 1e9 at the roof      */
+    double predicted_cu_gstencils; /* CU path at this t                      */
+    double predicted_tc_gstencils; /* TC path at this t (0 if not available) */
+} stencil_info;
+
+/* Input and output of the bare performance model (paper Sec. 3-4). */
+typedef struct {
+    int shape, d, r, t;
+    int dtype_bytes;   /* D */
+    double sparsity;   /* S */
+    double beta;       /* products per useful product */
+    double P_cu, P_tc, B;
+} stencil_model_in;
+
+typedef struct {
+    int K, K_fused;
+    double alpha;                 /* Eq. 9                                   */
+    double C_cu, C_tc, M;         /* FLOP and bytes per point and fused sweep */
+    double I_cu, I_tc;            /* Eq. 8, Eq. 12                           */
+    double ridge_cu, ridge_tc;
+    double P_cu_actual, P_tc_actual; /* useful FLOP/s (Eq. 8, Eq. 12)        */
+    double speedup;               /* P_TC,actual / P_CU,actual (Eq. 13)      */
+    int scenario;                 /* 1..4 (Sec. 4.1)                         */
+    int sweet_spot;               /* scenario 3, or 4 with Eq. 19 holding    */
+    double gstencils_cu, gstencils_tc; /* point-updates/s / 1e9 at the roofs */
+} stencil_model_out;
+
+typedef struct stencil_plan stencil_plan;
+
+/* ---- plans ------------------------------------------------------------- */
+
+/* Create a plan for `shape` (d in {2,3}, r >= 1) with K weights (copied;
+ * lexicographic offset order), element type `dtype`, interior extents
+ * dims[0..d-1] (slowest first, each >= 1) and fusion depth t (0 = let the
+ * model choose, else 1..16).  Host only: no CUDA call, no device memory.
+ * Defaults: path AUTO, precision NATIVE.  Errors: INVALID_ARG for a null or
+ * out-of-range argument, UNSUPPORTED when no kernel covers (shape, d, r). */
+stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int d, int r,
+                                   const double *weights, stencil_dtype dtype,
+                                   const int64_t *dims, int t);
+
+/* Set an option and re-run dispatch.  Keys and values:
+ *   "path"      auto | cuda_core | tensor_core | sparse_tensor_core
+ *   "precision" native | tf32 | tf32x3 | bf16x3 | any
+ *   "t"         0 (model) or 1..16
+ *   "tile"      "TYxTX" (2-D) or "TZxTYxTX" (3-D) output tile, "0" = default
+ * INVALID_ARG for an unknown key or value, UNSUPPORTED if the requested
+ * path/precision has no kernel for this plan (the plan is then unchanged). */
+stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, const char *value);
+
+/* What dispatch chose, with the model's predictions (host only). */
+stencil_status stencil_plan_info(const stencil_plan *plan, stencil_info *info);
+
+/* Bytes of device workspace stencil_run needs: one stored grid, used as
+ * the ping-pong buffer between fused sweeps (only touched when steps > t).
+ * With for_host_io != 0: what stencil_run_host needs (three grids: input,
+ * output, ping-pong). */
+size_t stencil_plan_workspace_bytes(const stencil_plan *plan, int for_host_io);
+
+/* Give the plan caller-owned device workspace (e.g. a PyTorch tensor); the
+ * plan keeps the pointer until replaced or destroyed and never frees it.
+ * INVALID_ARG if ptr is null with bytes > 0. */
+stencil_status stencil_plan_set_workspace(stencil_plan *plan, void *dev_ptr, size_t bytes);
+
+/* Run `steps` steps from `in` to `out` (device buffers of the stored size,
+ * halo included) on `stream`.  `in` is read only; its halo defines the fixed
+ * boundary and is copied to `out`.  steps = 0 copies in to out.  The run is
+ * ceil(steps/t) fused sweeps, the last one shorter if t does not divide
+ * steps.  INVALID_ARG if in == out, a pointer is null, or steps < 0; OOM if
+ * more than one sweep is needed and no workspace was set (the plan then
+ * allocates none itself).  Asynchronous: returns after enqueueing. */
+stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_t steps,
+                           stencil_stream_t stream);
+
+/* Same computation from host memory: copies host_in to the device,
+ * runs, copies the result to host_out, and synchronises `stream` before
+ * returning.  Needs stencil_plan_workspace_bytes(plan, 1) of workspace.
+ * Pinned host memory gives full copy bandwidth. */
+stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out,
+                                int64_t steps, stencil_stream_t stream);
+
+/* Release a plan (never frees caller workspace).  Null is ignored. */
+void stencil_plan_destroy(stencil_plan *plan);
+
+/* ---- model ------------------------------------------------------------- */
+
+/* The paper's model for one configuration (Sec. 3.2 Eqs. 6-12, Sec. 4.1
+ * Eqs. 13-19): K, K^(t), alpha, C, M, I, ridges, attainable rates,
+ * scenario and sweet spot.  Pure host arithmetic.  INVALID_ARG on null
+ * pointers, d outside 1..3, r < 1, t < 1, S outside (0, 1], a
+ * non-positive peak or bandwidth. */
+stencil_status stencil_model_predict(const stencil_model_in *in, stencil_model_out *out);
+
+/* Replace the process-wide peak table the dispatcher uses (zero fields
+ * unchanged) / read it.  Defaults are GB300 figures. */
+stencil_status stencil_set_peaks(const stencil_peaks *peaks);
+stencil_status stencil_get_peaks(stencil_peaks *peaks);
+
+/* ---- diagnostics ------------------------------------------------------- */
+
+const char *stencil_status_string(stencil_status s);
+const char *stencil_last_error(void);
+/* Kernel launches the calling thread has issued through this library since
+ * the process started (counted on the host at each launch). */
+uint64_t stencil_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

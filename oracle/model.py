@@ -10,19 +10,19 @@ redundancy factor alpha.
 
 * K: box (2r+1)^d (Sec. 3.2.1).  The paper writes no star count; a star has
   one centre and r points on each side of each axis, 2dr+1.
-* K^(t): number of points of the fused kernel.  Box: (2rt+1)^d (Eq. 9).  Star
+* K^(t): number of points of the fused kernel.  Box: (2rt+1)^d (Eq. 10).  Star
   (not given by the paper): the t-fold sum of star offsets is the set of p
   with sum_i ceil(|p_i|/r) <= t, whose size is
   sum_j C(d,j) C(t,j) (2r)^j.
 * C = 2K, M = 2D, I = K/D (Sec. 3.2.1).
 * CUDA cores with temporal fusion: C^(t) = tC, M^(t) = M, I = tK/D,
-  P = min(P_CU, B I) (Eq. 7).
-* Tensor cores with kernel fusion: C_TC^(t) = (alpha/S) C^(t) (Eq. 5),
-  alpha = K^(t)/(tK) (Eq. 8), I_TC = t (alpha/S) K/D,
-  P_TC,actual = (S/alpha) min(P_TC, B I_TC) (Eq. 11).
-* Speedup ratio and the four scenarios (Sec. 4.1, Eqs. 12-17); the sweet spot
+  P = min(P_CU, B I) (Eq. 8).
+* Tensor cores with kernel fusion: C_TC^(t) = (alpha/S) C^(t) (Eq. 3),
+  alpha = K^(t)/(tK) (Eq. 9), I_TC = t (alpha/S) K/D,
+  P_TC,actual = (S/alpha) min(P_TC, B I_TC) (Eq. 11-12).
+* Speedup ratio and the four scenarios (Sec. 4.1, Eqs. 13-19); the sweet spot
   is scenario 3 plus the part of scenario 4 where alpha < S P_TC/P_CU.
-* Sparse tensor cores: same intensity, peak P_SpTC (Sec. 4.3, Eq. 18).
+* Sparse tensor cores: same intensity, peak P_SpTC (Sec. 4.3, Eq. 20).
 
 One extension that is not in the paper: beta = products issued per useful
 product (1 for a single-precision MMA, 3 for hi/lo split forms), which
@@ -51,7 +51,7 @@ def K_fused(shape: str, d: int, r: int, t: int) -> int:
 
 
 def alpha(shape: str, d: int, r: int, t: int) -> float:
-    """Fusion redundancy factor alpha = K^(t) / (t K)  (Eq. 8)."""
+    """Fusion redundancy factor alpha = K^(t) / (t K)  (Eq. 9)."""
     return K_fused(shape, d, r, t) / (t * K_points(shape, d, r))
 
 
@@ -66,7 +66,7 @@ def M_point(D: int) -> float:
 
 
 def I_cu(shape, d, r, t, D) -> float:
-    """CUDA-core intensity with temporal fusion, I = t K / D  (Eq. 7)."""
+    """CUDA-core intensity with temporal fusion, I = t K / D  (Eq. 8)."""
     return t * K_points(shape, d, r) / D
 
 
@@ -75,17 +75,17 @@ def C_cu(shape, d, r, t) -> float:
 
 
 def C_tc(shape, d, r, t, S, beta=1.0) -> float:
-    """Executed tensor-core operations per fused point update (Eq. 5), times beta."""
+    """Executed tensor-core operations per fused point update (Eq. 3), times beta."""
     return beta * alpha(shape, d, r, t) / S * C_cu(shape, d, r, t)
 
 
 def I_tc(shape, d, r, t, D, S, beta=1.0) -> float:
-    """Tensor-core intensity I_TC = t (alpha/S) K/D  (Eq. 10-11), times beta."""
+    """Tensor-core intensity I_TC = t (alpha/S) K/D  (Eq. 11-12), times beta."""
     return beta * t * alpha(shape, d, r, t) / S * K_points(shape, d, r) / D
 
 
 def roofline(P_peak: float, B: float, I: float) -> float:
-    """P = min(P_peak, B I)  (Eq. 4)."""
+    """P = min(P_peak, B I)  (Eq. 5)."""
     return min(P_peak, B * I)
 
 
@@ -99,7 +99,7 @@ def P_cu_actual(shape, d, r, t, D, P_cu, B) -> float:
 
 
 def P_tc_actual(shape, d, r, t, D, S, P_tc, B, beta=1.0) -> float:
-    """(S / (alpha beta)) min(P_TC, B I_TC)  (Eq. 11; Eq. 18 with P_SpTC)."""
+    """(S / (alpha beta)) min(P_TC, B I_TC)  (Eq. 12; Eq. 20 with P_SpTC)."""
     a = alpha(shape, d, r, t)
     return S / (a * beta) * roofline(P_tc, B, I_tc(shape, d, r, t, D, S, beta))
 
@@ -117,12 +117,12 @@ def scenario(shape, d, r, t, D, S, P_cu, P_tc, B, beta=1.0) -> int:
 
 
 def speedup(shape, d, r, t, D, S, P_cu, P_tc, B, beta=1.0) -> float:
-    """P_TC,actual / P_CU,actual (Sec. 4.1, Eq. 12)."""
+    """P_TC,actual / P_CU,actual (Sec. 4.1, Eq. 13)."""
     return P_tc_actual(shape, d, r, t, D, S, P_tc, B, beta) / P_cu_actual(shape, d, r, t, D, P_cu, B)
 
 
 def alpha_condition(shape, d, r, t, S, P_cu, P_tc, beta=1.0) -> bool:
-    """alpha < S P_TC / P_CU (Eq. 17), with beta folded into alpha."""
+    """alpha < S P_TC / P_CU (Eq. 19), with beta folded into alpha."""
     return alpha(shape, d, r, t) * beta < S * P_tc / P_cu
 
 

@@ -16,7 +16,7 @@
  *   outermost, each coordinate ascending from -r; weights follow that order.
  *   The sum is formed in that order in FP64 (compiled with -ffp-contract=off).
  *
- * Temporal fusion (paper Sec. 2.2.3, kernel fusion; Eq. 8-9 for the fused
+ * Temporal fusion (paper Sec. 2.2.3, kernel fusion; Eq. 9-10 for the fused
  * support): t steps equal one application of the t-fold self-convolution
  * w^(t) (radius t*r) at points whose fused neighbourhood does not cross the
  * fixed halo.  oracle_compose builds w^(t) as a dense (2tr+1)^d box.

@@ -1,0 +1,298 @@
+"""Thin Python binding of libgbstencil's C ABI (include/gbstencil.h).
+
+Argument marshalling only: every step of the stencil runs in the library's
+CUDA kernels.  Functions carry the C names.  Device buffers are PyTorch CUDA
+tensors (their data pointers are passed through), streams are torch streams
+(or raw cudaStream_t integers).  There is no CPU fallback: if the compiled
+library is missing, loading fails with an error naming the build step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+_LIB = None
+
+STENCIL_OK, STENCIL_ERR_INVALID_ARG, STENCIL_ERR_UNSUPPORTED, STENCIL_ERR_CUDA, STENCIL_ERR_OOM, \
+    STENCIL_ERR_TIMEOUT = range(6)
+BOX, STAR = 0, 1
+F64, F32 = 0, 1
+PATH_AUTO, PATH_CUDA_CORE, PATH_TENSOR_CORE, PATH_SPARSE_TENSOR_CORE = range(4)
+PREC_NATIVE, PREC_TF32, PREC_TF32X3, PREC_BF16X3, PREC_ANY = range(5)
+PATH_NAMES = {0: "auto", 1: "cuda_core", 2: "tensor_core", 3: "sparse_tensor_core"}
+PREC_NAMES = {0: "native", 1: "tf32", 2: "tf32x3", 3: "bf16x3", 4: "any"}
+
+
+class StencilError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[{status}] {msg}")
+        self.status = status
+
+
+class stencil_peaks(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "hbm_bytes_per_s", "cu_f64_flops", "cu_f32_flops", "tc_f64_flops", "tc_tf32_flops", "tc_bf16_flops",
+        "sptc_tf32_flops", "sptc_bf16_flops")]
+
+
+class stencil_info(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("t", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("K", ctypes.c_int), ("K_fused", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("sparsity", ctypes.c_double), ("beta", ctypes.c_double),
+                ("intensity", ctypes.c_double), ("ridge", ctypes.c_double), ("scenario", ctypes.c_int),
+                ("memory_bound", ctypes.c_int), ("predicted_gstencils", ctypes.c_double),
+                ("predicted_cu_gstencils", ctypes.c_double), ("predicted_tc_gstencils", ctypes.c_double)]
+
+
+class stencil_model_in(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int), ("d", ctypes.c_int), ("r", ctypes.c_int), ("t", ctypes.c_int),
+                ("dtype_bytes", ctypes.c_int), ("sparsity", ctypes.c_double), ("beta", ctypes.c_double),
+                ("P_cu", ctypes.c_double), ("P_tc", ctypes.c_double), ("B", ctypes.c_double)]
+
+
+class stencil_model_out(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("K_fused", ctypes.c_int), ("alpha", ctypes.c_double),
+                ("C_cu", ctypes.c_double), ("C_tc", ctypes.c_double), ("M", ctypes.c_double),
+                ("I_cu", ctypes.c_double), ("I_tc", ctypes.c_double), ("ridge_cu", ctypes.c_double),
+                ("ridge_tc", ctypes.c_double), ("P_cu_actual", ctypes.c_double), ("P_tc_actual", ctypes.c_double),
+                ("speedup", ctypes.c_double), ("scenario", ctypes.c_int), ("sweet_spot", ctypes.c_int),
+                ("gstencils_cu", ctypes.c_double), ("gstencils_tc", ctypes.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load the in-tree libgbstencil.so (built by __graft_entry__.build())."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libgbstencil.so is not built ({path}); run `python -c 'import __graft_entry__ as g; "
+                          f"g.build()'` (needs nvcc, CUDA 13, sm_103a)")
+    L = ctypes.CDLL(path)
+    vp, i64, st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.stencil_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int]
+    L.stencil_plan_create.restype = st
+    L.stencil_plan_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
+    L.stencil_plan_set_option.restype = st
+    L.stencil_plan_info.argtypes = [vp, ctypes.POINTER(stencil_info)]
+    L.stencil_plan_info.restype = st
+    L.stencil_plan_workspace_bytes.argtypes = [vp, ctypes.c_int]
+    L.stencil_plan_workspace_bytes.restype = ctypes.c_size_t
+    L.stencil_plan_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.stencil_plan_set_workspace.restype = st
+    L.stencil_run.argtypes = [vp, vp, vp, i64, vp]
+    L.stencil_run.restype = st
+    L.stencil_run_host.argtypes = [vp, vp, vp, i64, vp]
+    L.stencil_run_host.restype = st
+    L.stencil_plan_destroy.argtypes = [vp]
+    L.stencil_plan_destroy.restype = None
+    L.stencil_model_predict.argtypes = [ctypes.POINTER(stencil_model_in), ctypes.POINTER(stencil_model_out)]
+    L.stencil_model_predict.restype = st
+    L.stencil_set_peaks.argtypes = [ctypes.POINTER(stencil_peaks)]
+    L.stencil_set_peaks.restype = st
+    L.stencil_get_peaks.argtypes = [ctypes.POINTER(stencil_peaks)]
+    L.stencil_get_peaks.restype = st
+    L.stencil_status_string.argtypes = [ctypes.c_int]
+    L.stencil_status_string.restype = ctypes.c_char_p
+    L.stencil_last_error.argtypes = []
+    L.stencil_last_error.restype = ctypes.c_char_p
+    L.stencil_launch_count.argtypes = []
+    L.stencil_launch_count.restype = ctypes.c_uint64
+    _LIB = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != STENCIL_OK:
+        msg = load().stencil_last_error().decode(errors="replace")
+        raise StencilError(status, f"{what}: {msg}")
+
+
+def _shape_code(shape) -> int:
+    if isinstance(shape, str):
+        return {"box": BOX, "star": STAR}[shape.lower()]
+    return int(shape)
+
+
+def _dtype_code(dtype) -> int:
+    s = str(dtype)
+    if s in ("f64", "float64", "torch.float64", "double", "0"):
+        return F64
+    if s in ("f32", "float32", "torch.float32", "float", "1"):
+        return F32
+    raise ValueError(f"dtype {dtype!r}: use f64 or f32")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C names ------------------------------------------------------------------
+
+def stencil_plan_create(shape, d: int, r: int, weights, dtype, dims, t: int = 0) -> int:
+    w = (ctypes.c_double * len(weights))(*[float(x) for x in weights])
+    dd = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    h = ctypes.c_void_p()
+    _check(load().stencil_plan_create(ctypes.byref(h), _shape_code(shape), int(d), int(r), w, _dtype_code(dtype), dd,
+                                      int(t)), "stencil_plan_create")
+    return h.value
+
+
+def stencil_plan_set_option(plan: int, key: str, value) -> None:
+    _check(load().stencil_plan_set_option(plan, key.encode(), str(value).encode()), f"stencil_plan_set_option({key})")
+
+
+def stencil_plan_info(plan: int) -> dict:
+    info = stencil_info()
+    _check(load().stencil_plan_info(plan, ctypes.byref(info)), "stencil_plan_info")
+    out = {f: getattr(info, f) for f, _ in stencil_info._fields_}
+    out["tile"] = list(info.tile)
+    out["path_name"] = PATH_NAMES[info.path]
+    out["precision_name"] = PREC_NAMES[info.precision]
+    return out
+
+
+def stencil_plan_workspace_bytes(plan: int, for_host_io: bool = False) -> int:
+    return int(load().stencil_plan_workspace_bytes(plan, 1 if for_host_io else 0))
+
+
+def stencil_plan_set_workspace(plan: int, dev_ptr: int, nbytes: int) -> None:
+    _check(load().stencil_plan_set_workspace(plan, dev_ptr, nbytes), "stencil_plan_set_workspace")
+
+
+def stencil_run(plan: int, in_ptr: int, out_ptr: int, steps: int, stream=None) -> None:
+    _check(load().stencil_run(plan, in_ptr, out_ptr, int(steps), _stream_handle(stream)), "stencil_run")
+
+
+def stencil_run_host(plan: int, host_in_ptr: int, host_out_ptr: int, steps: int, stream=None) -> None:
+    _check(load().stencil_run_host(plan, host_in_ptr, host_out_ptr, int(steps), _stream_handle(stream)),
+           "stencil_run_host")
+
+
+def stencil_plan_destroy(plan: int) -> None:
+    if plan:
+        load().stencil_plan_destroy(plan)
+
+
+def stencil_model_predict(shape, d, r, t, dtype_bytes, sparsity, beta, P_cu, P_tc, B) -> dict:
+    q = stencil_model_in(_shape_code(shape), d, r, t, dtype_bytes, sparsity, beta, P_cu, P_tc, B)
+    o = stencil_model_out()
+    _check(load().stencil_model_predict(ctypes.byref(q), ctypes.byref(o)), "stencil_model_predict")
+    return {f: getattr(o, f) for f, _ in stencil_model_out._fields_}
+
+
+def stencil_set_peaks(**kw) -> None:
+    p = stencil_peaks(**kw)
+    _check(load().stencil_set_peaks(ctypes.byref(p)), "stencil_set_peaks")
+
+
+def stencil_get_peaks() -> dict:
+    p = stencil_peaks()
+    _check(load().stencil_get_peaks(ctypes.byref(p)), "stencil_get_peaks")
+    return {f: getattr(p, f) for f, _ in stencil_peaks._fields_}
+
+
+def stencil_status_string(s: int) -> str:
+    return load().stencil_status_string(s).decode()
+
+
+def stencil_last_error() -> str:
+    return load().stencil_last_error().decode(errors="replace")
+
+
+def stencil_launch_count() -> int:
+    return int(load().stencil_launch_count())
+
+
+def declared_symbols(header: str | None = None) -> list[str]:
+    """Function names declared in include/gbstencil.h."""
+    header = header or os.path.join(_build.INCLUDE, "gbstencil.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(stencil_[a-z0-9_]+)\s*\(", text)))
+
+
+# ---- convenience wrapper over torch tensors ----------------------------------------
+
+class Plan:
+    """A plan plus PyTorch-allocated workspace.  run() takes CUDA tensors of
+    the stored shape (interior + 2r per axis) and the plan's dtype."""
+
+    def __init__(self, shape, d, r, weights, dtype, dims, t: int = 0, **options):
+        self.shape, self.d, self.r = shape, int(d), int(r)
+        self.dims = tuple(int(x) for x in dims)
+        self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
+        self.handle = stencil_plan_create(shape, d, r, weights, dtype, dims, t)
+        self._ws = None
+        for k, v in options.items():
+            stencil_plan_set_option(self.handle, k, v)
+
+    @property
+    def stored_shape(self):
+        return tuple(n + 2 * self.r for n in self.dims)
+
+    def set_option(self, key, value):
+        stencil_plan_set_option(self.handle, key, value)
+
+    def info(self) -> dict:
+        return stencil_plan_info(self.handle)
+
+    def _torch_dtype(self):
+        import torch
+        return torch.float64 if self.dtype == "f64" else torch.float32
+
+    def ensure_workspace(self, device, host_io: bool = False):
+        import torch
+        need = stencil_plan_workspace_bytes(self.handle, host_io)
+        if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device(device):
+            self._ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+            stencil_plan_set_workspace(self.handle, self._ws.data_ptr(), self._ws.numel())
+        return self._ws
+
+    def _check_tensor(self, x, name):
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if x.dtype != self._torch_dtype() or not x.is_contiguous() or tuple(x.shape) != self.stored_shape:
+            raise ValueError(f"{name}: need a contiguous {self._torch_dtype()} tensor of shape {self.stored_shape}")
+
+    def run(self, x_in, x_out, steps: int, stream=None):
+        self._check_tensor(x_in, "in")
+        self._check_tensor(x_out, "out")
+        self.ensure_workspace(x_in.device)
+        stencil_run(self.handle, x_in.data_ptr(), x_out.data_ptr(), steps, stream)
+
+    def run_host(self, h_in, h_out, steps: int, device="cuda", stream=None):
+        """h_in/h_out: CPU tensors (pinned for full speed) of the stored shape."""
+        import torch
+        for x, n in ((h_in, "host in"), (h_out, "host out")):
+            if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != self._torch_dtype() \
+                    or not x.is_contiguous() or tuple(x.shape) != self.stored_shape:
+                raise ValueError(f"{n}: need a contiguous CPU {self._torch_dtype()} tensor of shape "
+                                 f"{self.stored_shape}")
+        self.ensure_workspace(device, host_io=True)
+        stencil_run_host(self.handle, h_in.data_ptr(), h_out.data_ptr(), steps, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stencil_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,244 @@
+// cu_kernels.cuh -- CUDA-core stencil sweeps with temporal blocking.
+//
+// Paper Sec. 3.2.2 (CUDA cores with temporal fusion): t steps are fused in
+// one pass over the grid; the intermediate steps never leave the SM, so the
+// HBM traffic per point stays one read and one write (M = 2D) while the
+// arithmetic grows to t * 2K (Eq. 8).
+//
+// One CTA owns an output tile.  It stages the tile grown by t*r on every
+// side (the dependency region of t steps) from global memory into shared
+// memory, then runs the t sub-steps in shared memory (ping-pong between two
+// buffers); sub-step s computes the region grown by (t - s) r.  Points that
+// are not interior (the fixed halo, or outside the stored array) keep their
+// value, which re-imposes the Dirichlet boundary after every sub-step.  The
+// last sub-step writes straight to global memory.  Each thread computes a
+// strip of V outputs along the slowest tile axis and reuses every loaded
+// input row/plane across the strip from registers.
+//
+// Weights are kernel parameters (constant bank), K values in the library's
+// lexicographic offset order.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace gbs {
+namespace cu {
+
+constexpr int kThreads = 256;
+
+template <int SHAPE, int D, int R>
+struct Taps {
+    static constexpr int side = 2 * R + 1;
+    static constexpr int K = SHAPE == 0 ? (D == 2 ? side * side : side * side * side) : 2 * D * R + 1;
+};
+
+// Index of offset (oz, oy, ox) in the lexicographic offset list, -1 if the
+// offset is not part of the pattern.  D == 2 ignores oz.
+template <int SHAPE, int D, int R>
+__host__ __device__ constexpr int tap_index(int oz, int oy, int ox)
+{
+    if (SHAPE == 0) {
+        return D == 2 ? (oy + R) * (2 * R + 1) + (ox + R)
+                      : ((oz + R) * (2 * R + 1) + (oy + R)) * (2 * R + 1) + (ox + R);
+    }
+    const int nz = (D == 3 && oz != 0) + (oy != 0) + (ox != 0);
+    if (nz > 1) return -1;
+    if (D == 2) {
+        if (oy < 0) return oy + R;
+        if (oy == 0) return 2 * R + ox;
+        return 3 * R + oy;
+    }
+    if (oz < 0) return oz + R;
+    if (oz == 0) {
+        if (oy < 0) return R + oy + R;
+        if (oy == 0) return 3 * R + ox;
+        return 4 * R + oy;
+    }
+    return 5 * R + oz;
+}
+
+template <typename T, int K>
+struct Weights {
+    T w[K];
+};
+
+// ---------------------------------------------------------------------------
+// 2-D: tile BY x BX, strips of V rows.
+// ---------------------------------------------------------------------------
+template <typename T, int SHAPE, int R, int V>
+__global__ void __launch_bounds__(kThreads)
+    cu2d_sweep(const T *__restrict__ in, T *__restrict__ out, const Weights<T, Taps<SHAPE, 2, R>::K> wt,
+               int64_t Ey, int64_t Ex, int BY, int BX, int t)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = BY + 2 * t * R, W = BX + 2 * t * R;
+    T *bufA = reinterpret_cast<T *>(smem_raw);
+    T *bufB = bufA + (size_t)H * W;
+    const int64_t Y0 = R + (int64_t)blockIdx.y * BY - (int64_t)t * R;
+    const int64_t X0 = R + (int64_t)blockIdx.x * BX - (int64_t)t * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+
+    // Stage the dependency region; cells outside the stored array read 0
+    // and are never used by an interior point.
+    for (int y = warp; y < H; y += nwarps) {
+        const int64_t gy = Y0 + y;
+        const bool rowok = gy >= 0 && gy < Ey;
+        const T *src = in + gy * Ex;
+        for (int x = lane; x < W; x += 32) {
+            const int64_t gx = X0 + x;
+            bufA[y * W + x] = (rowok && gx >= 0 && gx < Ex) ? __ldg(src + gx) : T(0);
+        }
+    }
+    __syncthreads();
+
+    T *src = bufA, *dst = bufB;
+    for (int s = 1; s <= t; ++s) {
+        const int lo = s * R;
+        const int hiY = H - s * R, hiX = W - s * R;
+        const int cw = hiX - lo, ch = hiY - lo;
+        const int strips = (ch + V - 1) / V;
+        const bool last = s == t;
+        for (int item = threadIdx.x; item < cw * strips; item += blockDim.x) {
+            const int x = lo + item % cw;
+            const int y0 = lo + (item / cw) * V;
+            T acc[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) acc[j] = T(0);
+#pragma unroll
+            for (int q = 0; q < V + 2 * R; ++q) {
+                const int yy = y0 - R + q;
+                if (yy < H) {
+                    const T *row = src + yy * W + x;
+                    T v[2 * R + 1];
+#pragma unroll
+                    for (int c = 0; c < 2 * R + 1; ++c) v[c] = row[c - R];
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        const int oy = q - R - j;
+                        if (oy >= -R && oy <= R) {
+#pragma unroll
+                            for (int ox = -R; ox <= R; ++ox) {
+                                const int k = tap_index<SHAPE, 2, R>(0, oy, ox);
+                                if (k >= 0) acc[j] = fma(wt.w[k], v[ox + R], acc[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            const int64_t gx = X0 + x;
+            const bool colint = gx >= R && gx < Ex - R;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int y = y0 + j;
+                if (y < hiY) {
+                    const int64_t gy = Y0 + y;
+                    const bool interior = colint && gy >= R && gy < Ey - R;
+                    if (last) {
+                        if (interior) out[gy * Ex + gx] = acc[j];
+                    } else {
+                        dst[y * W + x] = interior ? acc[j] : src[y * W + x];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        T *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3-D: tile BZ x BY x BX, strips of V planes.
+// ---------------------------------------------------------------------------
+template <typename T, int SHAPE, int R, int V>
+__global__ void __launch_bounds__(kThreads)
+    cu3d_sweep(const T *__restrict__ in, T *__restrict__ out, const Weights<T, Taps<SHAPE, 3, R>::K> wt,
+               int64_t Ez, int64_t Ey, int64_t Ex, int BZ, int BY, int BX, int t, int tiles_x)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Z = BZ + 2 * t * R, H = BY + 2 * t * R, W = BX + 2 * t * R;
+    const int plane = H * W;
+    T *bufA = reinterpret_cast<T *>(smem_raw);
+    T *bufB = bufA + (size_t)Z * plane;
+    const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+    const int64_t Z0 = R + (int64_t)blockIdx.y * BZ - (int64_t)t * R;
+    const int64_t Y0 = R + (int64_t)by * BY - (int64_t)t * R;
+    const int64_t X0 = R + (int64_t)bx * BX - (int64_t)t * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+
+    for (int zy = warp; zy < Z * H; zy += nwarps) {
+        const int z = zy / H, y = zy % H;
+        const int64_t gz = Z0 + z, gy = Y0 + y;
+        const bool ok = gz >= 0 && gz < Ez && gy >= 0 && gy < Ey;
+        const T *src = in + (gz * Ey + gy) * Ex;
+        for (int x = lane; x < W; x += 32) {
+            const int64_t gx = X0 + x;
+            bufA[z * plane + y * W + x] = (ok && gx >= 0 && gx < Ex) ? __ldg(src + gx) : T(0);
+        }
+    }
+    __syncthreads();
+
+    T *src = bufA, *dst = bufB;
+    for (int s = 1; s <= t; ++s) {
+        const int lo = s * R;
+        const int hiZ = Z - s * R, hiY = H - s * R, hiX = W - s * R;
+        const int cw = hiX - lo, ch = hiY - lo, cz = hiZ - lo;
+        const int strips = (cz + V - 1) / V;
+        const bool last = s == t;
+        for (int item = threadIdx.x; item < cw * ch * strips; item += blockDim.x) {
+            const int x = lo + item % cw;
+            const int y = lo + (item / cw) % ch;
+            const int z0 = lo + (item / (cw * ch)) * V;
+            T acc[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) acc[j] = T(0);
+#pragma unroll
+            for (int q = 0; q < V + 2 * R; ++q) {
+                const int zz = z0 - R + q;
+                if (zz < Z) {
+                    const T *pl = src + zz * plane + y * W + x;
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        const int oz = q - R - j;
+                        if (oz >= -R && oz <= R) {
+#pragma unroll
+                            for (int oy = -R; oy <= R; ++oy) {
+#pragma unroll
+                                for (int ox = -R; ox <= R; ++ox) {
+                                    const int k = tap_index<SHAPE, 3, R>(oz, oy, ox);
+                                    if (k >= 0) acc[j] = fma(wt.w[k], pl[oy * W + ox], acc[j]);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            const int64_t gx = X0 + x, gy = Y0 + y;
+            const bool lineint = gx >= R && gx < Ex - R && gy >= R && gy < Ey - R;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int z = z0 + j;
+                if (z < hiZ) {
+                    const int64_t gz = Z0 + z;
+                    const bool interior = lineint && gz >= R && gz < Ez - R;
+                    if (last) {
+                        if (interior) out[(gz * Ey + gy) * Ex + gx] = acc[j];
+                    } else {
+                        const int o = z * plane + y * W + x;
+                        dst[o] = interior ? acc[j] : src[o];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        T *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+}
+
+}  // namespace cu
+}  // namespace gbs

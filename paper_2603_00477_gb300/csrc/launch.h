@@ -1,0 +1,23 @@
+// launch.h -- kernel launchers of libgbstencil (host side, CUDA runtime).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace gbs {
+
+// One fused sweep of depth t on the CUDA-core path from in to out (interior
+// points only; halo cells of out are left untouched).
+stencil_status launch_cu_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
+
+// Copy the halo cells (the fixed boundary) of `in` to `out` and, if not null,
+// to `out2`.
+stencil_status launch_halo_copy(const Plan &p, const void *in, void *out, void *out2, cudaStream_t st);
+
+// Raise the dynamic shared-memory limit of `func` to `bytes` once.
+stencil_status ensure_smem(const void *func, size_t bytes, int *cached);
+
+stencil_status cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace gbs

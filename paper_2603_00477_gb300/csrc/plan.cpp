@@ -1,0 +1,441 @@
+// plan.cpp -- plan creation, options, dispatch and diagnostics (host only).
+//
+// Dispatch is the paper's model used as a decision rule: for every
+// available (path, precision, t) the attainable point-update rate is
+// min(P S / (2K alpha beta), t B / (2D)) (Eq. 8 for CUDA cores, Eq. 12 for
+// tensor cores, Eq. 20 with the sparse peak), the CUDA-core compute term
+// being divided by the redundant work of overlapped temporal tiles (the
+// halo overlap the paper leaves out of its model).  The fastest candidate
+// wins; candidates within 2 % of it are ordered CUDA cores first (no
+// redundancy), then smaller t, then fewer products.
+#include <algorithm>
+#include <atomic>
+#include <cctype>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace gbs {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+stencil_status fail(stencil_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+void note_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Radii the CUDA-core kernels are instantiated for (k_cuda_core*.cu).
+bool cu_supported(int shape, int d, int r)
+{
+    if (d == 2) return r >= 1 && r <= 7;
+    if (d == 3) return shape == STENCIL_BOX ? (r >= 1 && r <= 2) : (r >= 1 && r <= 4);
+    return false;
+}
+
+static int max_fused_t(const Plan &p, int path)
+{
+    if (path == STENCIL_PATH_CUDA_CORE) return p.pat.d == 2 ? 4 : 2;
+    return 4;
+}
+
+void cu_default_tile(const Plan &p, int t, int tile[3])
+{
+    const int R = p.pat.r;
+    if (p.pat.d == 2) {
+        tile[0] = 1;
+        tile[1] = 64;
+        tile[2] = p.dtype == STENCIL_F64 ? 64 : 128;
+        // keep two smem buffers under ~200 KB
+        for (;;) {
+            size_t h = tile[1] + 2 * t * R, w = tile[2] + 2 * t * R;
+            size_t bytes = h * w * p.elem_bytes() * (t > 1 ? 2 : 1);
+            if (bytes <= 200 * 1024 || tile[2] <= 32) break;
+            if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
+        }
+    } else {
+        tile[0] = 8;
+        tile[1] = 8;
+        tile[2] = 32;
+        for (;;) {
+            size_t z = tile[0] + 2 * t * R, h = tile[1] + 2 * t * R, w = tile[2] + 2 * t * R;
+            size_t bytes = z * h * w * p.elem_bytes() * (t > 1 ? 2 : 1);
+            if (bytes <= 200 * 1024 || tile[0] <= 2) break;
+            tile[0] /= 2;
+        }
+    }
+}
+
+// Issued-work factor of overlapped temporal tiles: sub-step s computes the
+// tile grown by (t - s) r on every side.
+static double cu_overlap_factor(const Plan &p, int t, const int tile[3])
+{
+    const int d = p.pat.d, r = p.pat.r;
+    double issued = 0, useful = (double)t;
+    for (int s = 1; s <= t; s++) {
+        double v = 1;
+        for (int i = 3 - d; i < 3; i++) v *= (double)(tile[i] + 2 * (t - s) * r) / tile[i];
+        issued += v;
+    }
+    return issued / useful;
+}
+
+// Lines (rows in 2-D, (plane,row) pairs in 3-D) of the composite kernel and
+// the half-width of each: box lines are all R wide; a star line at plane c,
+// row a holds |b| <= r (t - ceil|c|/r - ceil|a|/r).
+static void composite_lines(int shape, int d, int r, int t, std::vector<int> *half)
+{
+    half->clear();
+    const int R = t * r;
+    auto ce = [r](int v) { return (std::abs(v) + r - 1) / r; };
+    if (d == 2) {
+        for (int a = -R; a <= R; a++) {
+            if (shape == STENCIL_BOX) half->push_back(R);
+            else half->push_back(r * (t - ce(a)));
+        }
+    } else {
+        for (int c = -R; c <= R; c++)
+            for (int a = -R; a <= R; a++) {
+                if (shape == STENCIL_BOX) half->push_back(R);
+                else if (ce(c) + ce(a) <= t) half->push_back(r * (t - ce(c) - ce(a)));
+            }
+    }
+}
+
+TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int precision, int path)
+{
+    TcGeometry g;
+    g.n_tile = 8;
+    if (dtype == STENCIL_F64) g.k_inst = 4;                 // FP64 MMA m8n8k4
+    else if (precision == STENCIL_PREC_BF16X3) g.k_inst = 16;  // kind::f16 K = 16
+    else g.k_inst = 8;                                      // kind::tf32 K = 8
+    std::vector<int> half;
+    composite_lines(shape, d, r, t, &half);
+    double useful = 0, issued = 0;
+    int kmax = 0;
+    for (int h : half) {
+        int kext = (g.n_tile + 2 * h + g.k_inst - 1) / g.k_inst * g.k_inst;
+        useful += 2 * h + 1;
+        issued += kext;
+        kmax = std::max(kmax, kext);
+    }
+    g.kext = kmax;
+    g.sparsity = issued > 0 ? useful / issued : 0;
+    (void)path;
+    return g;
+}
+
+// Tensor-core kernels present in this build.
+bool tc_supported(const Plan &p, int precision, int path)
+{
+    (void)p;
+    (void)precision;
+    (void)path;
+    return false;
+}
+
+static double tc_peak(const Plan &p, int precision, int path)
+{
+    const stencil_peaks &pk = peaks();
+    const bool sparse = path == STENCIL_PATH_SPARSE_TENSOR_CORE;
+    if (p.dtype == STENCIL_F64) return pk.tc_f64_flops;
+    if (precision == STENCIL_PREC_BF16X3) return sparse ? pk.sptc_bf16_flops : pk.tc_bf16_flops;
+    return sparse ? pk.sptc_tf32_flops : pk.tc_tf32_flops;
+}
+
+static double beta_of(int precision)
+{
+    return (precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3) ? 3.0 : 1.0;
+}
+
+stencil_status dispatch(Plan *p)
+{
+    const stencil_peaks &pk = peaks();
+    const int D = (int)p->elem_bytes();
+    const int shape = p->pat.shape, d = p->pat.d, r = p->pat.r;
+    const double P_cu = p->dtype == STENCIL_F64 ? pk.cu_f64_flops : pk.cu_f32_flops;
+    const double B = pk.hbm_bytes_per_s;
+
+    std::vector<int> precs;
+    if (p->req_precision == STENCIL_PREC_ANY) {
+        precs.push_back(STENCIL_PREC_NATIVE);
+        if (p->dtype == STENCIL_F32) {
+            precs.push_back(STENCIL_PREC_TF32);
+            precs.push_back(STENCIL_PREC_TF32X3);
+            precs.push_back(STENCIL_PREC_BF16X3);
+        }
+    } else {
+        precs.push_back(p->req_precision);
+    }
+    std::vector<int> paths;
+    if (p->req_path == STENCIL_PATH_AUTO) {
+        paths = {STENCIL_PATH_CUDA_CORE, STENCIL_PATH_TENSOR_CORE, STENCIL_PATH_SPARSE_TENSOR_CORE};
+    } else {
+        paths = {p->req_path};
+    }
+
+    struct Cand {
+        int path, prec, t;
+        double gst;
+        int tile[3];
+    };
+    std::vector<Cand> cands;
+    for (int path : paths) {
+        for (int prec : precs) {
+            if (path == STENCIL_PATH_CUDA_CORE) {
+                if (prec != STENCIL_PREC_NATIVE || !cu_supported(shape, d, r)) continue;
+            } else {
+                if (p->dtype == STENCIL_F32 && prec == STENCIL_PREC_NATIVE) continue;  // no FP32 MMA
+                if (!tc_supported(*p, prec, path)) continue;
+            }
+            int t_lo = p->req_t ? p->req_t : 1;
+            int t_hi = p->req_t ? p->req_t : max_fused_t(*p, path);
+            for (int t = t_lo; t <= t_hi; t++) {
+                Cand c{path, prec, t, 0.0, {1, 1, 1}};
+                if (path == STENCIL_PATH_CUDA_CORE) {
+                    if (p->req_tile[0] || p->req_tile[1] || p->req_tile[2]) {
+                        for (int i = 0; i < 3; i++) c.tile[i] = p->req_tile[i] ? p->req_tile[i] : 1;
+                    } else {
+                        cu_default_tile(*p, t, c.tile);
+                    }
+                    ModelOut m = model_eval(shape, d, r, t, D, 1.0, 1.0, P_cu, P_cu, B);
+                    double ovl = cu_overlap_factor(*p, t, c.tile);
+                    double comp = P_cu / (2.0 * m.K) / ovl / 1e9;
+                    double mem = t * B / (2.0 * D) / 1e9;
+                    c.gst = std::min(comp, mem);
+                } else {
+                    TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
+                    ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec), P_cu,
+                                            tc_peak(*p, prec, path), B);
+                    c.gst = m.gst_tc;
+                }
+                cands.push_back(c);
+            }
+        }
+    }
+    if (cands.empty())
+        return fail(STENCIL_ERR_UNSUPPORTED, "no kernel for this (path, precision, shape, d, r, dtype)");
+    double best = 0;
+    for (auto &c : cands) best = std::max(best, c.gst);
+    const Cand *pick = nullptr;
+    for (auto &c : cands) {
+        if (c.gst < 0.98 * best) continue;
+        if (!pick) {
+            pick = &c;
+            continue;
+        }
+        auto key = [](const Cand &x) {
+            return std::make_tuple(x.path == STENCIL_PATH_CUDA_CORE ? 0 : 1, x.t, beta_of(x.prec));
+        };
+        if (key(c) < key(*pick)) pick = &c;
+    }
+
+    p->path = pick->path;
+    p->precision = pick->prec;
+    p->t = pick->t;
+    for (int i = 0; i < 3; i++) p->tile[i] = pick->tile[i];
+
+    // info: the model at the chosen t for both units
+    stencil_info &in = p->info;
+    std::memset(&in, 0, sizeof(in));
+    in.path = p->path;
+    in.precision = p->precision;
+    in.t = p->t;
+    for (int i = 0; i < 3; i++) in.tile[i] = p->tile[i];
+    const int tc_prec = p->dtype == STENCIL_F64 ? STENCIL_PREC_NATIVE
+                        : (p->precision == STENCIL_PREC_NATIVE ? STENCIL_PREC_TF32 : p->precision);
+    const int tc_path = p->path == STENCIL_PATH_CUDA_CORE ? STENCIL_PATH_TENSOR_CORE : p->path;
+    TcGeometry g = tc_geometry(shape, d, r, p->t, p->dtype, tc_prec, tc_path);
+    ModelOut m = model_eval(shape, d, r, p->t, D, g.sparsity, beta_of(tc_prec), P_cu,
+                            tc_peak(*p, tc_prec, tc_path), B);
+    in.K = m.K;
+    in.K_fused = m.K_fused;
+    in.scenario = m.scenario;
+    in.predicted_cu_gstencils = m.gst_cu;
+    in.predicted_tc_gstencils = tc_supported(*p, tc_prec, tc_path) ? m.gst_tc : 0.0;
+    in.predicted_gstencils = pick->gst;
+    if (p->path == STENCIL_PATH_CUDA_CORE) {
+        in.alpha = 1.0;
+        in.sparsity = 1.0;
+        in.beta = 1.0;
+        in.intensity = m.I_cu;
+        in.ridge = m.ridge_cu;
+        in.memory_bound = m.I_cu < m.ridge_cu;
+    } else {
+        in.alpha = m.alpha;
+        in.sparsity = g.sparsity;
+        in.beta = beta_of(tc_prec);
+        in.intensity = m.I_tc;
+        in.ridge = m.ridge_tc;
+        in.memory_bound = m.I_tc < m.ridge_tc;
+    }
+    return STENCIL_OK;
+}
+
+static bool parse_int(const char *s, long *out)
+{
+    if (!s || !*s) return false;
+    char *end = nullptr;
+    long v = std::strtol(s, &end, 10);
+    if (*end != '\0') return false;
+    *out = v;
+    return true;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" {
+
+stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int d, int r,
+                                   const double *weights, stencil_dtype dtype, const int64_t *dims, int t)
+{
+    if (!plan) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: plan is null");
+    *plan = nullptr;
+    if (!weights || !dims) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: weights or dims is null");
+    if (shape != STENCIL_BOX && shape != STENCIL_STAR)
+        return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: shape must be BOX or STAR");
+    if (d != 2 && d != 3) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: d must be 2 or 3");
+    if (r < 1 || r > 64) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: r must be in 1..64");
+    if (dtype != STENCIL_F64 && dtype != STENCIL_F32)
+        return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: dtype must be F64 or F32");
+    if (t < 0 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: t must be in 0..16");
+    Plan p;
+    if (!make_pattern(shape, d, r, &p.pat)) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: pattern");
+    p.dtype = dtype;
+    int64_t n_int = 1, n_st = 1;
+    for (int i = 0; i < 3; i++) {
+        p.dims[i] = 1;
+        p.ext[i] = 1;
+    }
+    for (int i = 0; i < d; i++) {
+        if (dims[i] < 1 || dims[i] > (int64_t)1 << 31)
+            return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: every extent must be in 1..2^31");
+        p.dims[3 - d + i] = dims[i];
+        p.ext[3 - d + i] = dims[i] + 2 * r;
+        n_int *= dims[i];
+        n_st *= dims[i] + 2 * r;
+        if (n_st > ((int64_t)1 << 40))
+            return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: grid larger than 2^40 elements");
+    }
+    p.n_interior = n_int;
+    p.n_stored = n_st;
+    p.w.assign(weights, weights + p.pat.K);
+    for (double x : p.w)
+        if (!std::isfinite(x)) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: weight not finite");
+    p.req_t = t;
+    if (!cu_supported(shape, d, r))
+        return fail(STENCIL_ERR_UNSUPPORTED, "stencil_plan_create: no CUDA-core kernel for this (shape, d, r)");
+    stencil_status s = dispatch(&p);
+    if (s != STENCIL_OK) return s;
+    stencil_plan *out = new (std::nothrow) stencil_plan;
+    if (!out) return fail(STENCIL_ERR_OOM, "stencil_plan_create: host allocation failed");
+    out->p = std::move(p);
+    *plan = out;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, const char *value)
+{
+    if (!plan || !key || !value) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_option: null argument");
+    Plan trial = plan->p;
+    std::string k(key), v(value);
+    if (k == "path") {
+        if (v == "auto") trial.req_path = STENCIL_PATH_AUTO;
+        else if (v == "cuda_core") trial.req_path = STENCIL_PATH_CUDA_CORE;
+        else if (v == "tensor_core") trial.req_path = STENCIL_PATH_TENSOR_CORE;
+        else if (v == "sparse_tensor_core") trial.req_path = STENCIL_PATH_SPARSE_TENSOR_CORE;
+        else return fail(STENCIL_ERR_INVALID_ARG, "path must be auto|cuda_core|tensor_core|sparse_tensor_core");
+    } else if (k == "precision") {
+        if (v == "native") trial.req_precision = STENCIL_PREC_NATIVE;
+        else if (v == "tf32") trial.req_precision = STENCIL_PREC_TF32;
+        else if (v == "tf32x3") trial.req_precision = STENCIL_PREC_TF32X3;
+        else if (v == "bf16x3") trial.req_precision = STENCIL_PREC_BF16X3;
+        else if (v == "any") trial.req_precision = STENCIL_PREC_ANY;
+        else return fail(STENCIL_ERR_INVALID_ARG, "precision must be native|tf32|tf32x3|bf16x3|any");
+        if (trial.dtype == STENCIL_F64 && trial.req_precision != STENCIL_PREC_NATIVE &&
+            trial.req_precision != STENCIL_PREC_ANY)
+            return fail(STENCIL_ERR_INVALID_ARG, "FP64 grids take precision native or any");
+    } else if (k == "t") {
+        long t = 0;
+        if (!parse_int(value, &t) || t < 0 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "t must be 0..16");
+        trial.req_t = (int)t;
+    } else if (k == "tile") {
+        int tl[3] = {0, 0, 0};
+        if (v != "0") {
+            int a = 0, b = 0, c = 0;
+            char extra = 0;
+            int n = std::sscanf(value, "%dx%dx%d%c", &a, &b, &c, &extra);
+            if (trial.pat.d == 3 && n == 3 && a > 0 && b > 0 && c > 0) {
+                tl[0] = a;
+                tl[1] = b;
+                tl[2] = c;
+            } else if (trial.pat.d == 2 && std::sscanf(value, "%dx%d%c", &a, &b, &extra) == 2 && a > 0 && b > 0) {
+                tl[0] = 1;
+                tl[1] = a;
+                tl[2] = b;
+            } else {
+                return fail(STENCIL_ERR_INVALID_ARG, "tile must be TYxTX (2-D) or TZxTYxTX (3-D)");
+            }
+            if (tl[2] % 4 != 0 || tl[2] > 1024 || tl[1] > 1024 || tl[0] > 1024)
+                return fail(STENCIL_ERR_INVALID_ARG, "tile: TX must be a multiple of 4, sides <= 1024");
+        }
+        for (int i = 0; i < 3; i++) trial.req_tile[i] = tl[i];
+    } else {
+        return fail(STENCIL_ERR_INVALID_ARG, "unknown option key '" + k + "'");
+    }
+    stencil_status s = dispatch(&trial);
+    if (s != STENCIL_OK) return s;
+    plan->p = std::move(trial);
+    return STENCIL_OK;
+}
+
+stencil_status stencil_plan_info(const stencil_plan *plan, stencil_info *info)
+{
+    if (!plan || !info) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_info: null argument");
+    *info = plan->p.info;
+    return STENCIL_OK;
+}
+
+size_t stencil_plan_workspace_bytes(const stencil_plan *plan, int for_host_io)
+{
+    if (!plan) return 0;
+    return plan->p.grid_bytes() * (for_host_io ? 3 : 1);
+}
+
+stencil_status stencil_plan_set_workspace(stencil_plan *plan, void *dev_ptr, size_t bytes)
+{
+    if (!plan) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_workspace: plan is null");
+    if (!dev_ptr && bytes > 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_workspace: null with bytes > 0");
+    plan->p.ws = dev_ptr;
+    plan->p.ws_bytes = dev_ptr ? bytes : 0;
+    return STENCIL_OK;
+}
+
+void stencil_plan_destroy(stencil_plan *plan) { delete plan; }
+
+const char *stencil_status_string(stencil_status s)
+{
+    switch (s) {
+    case STENCIL_OK: return "ok";
+    case STENCIL_ERR_INVALID_ARG: return "invalid argument";
+    case STENCIL_ERR_UNSUPPORTED: return "unsupported";
+    case STENCIL_ERR_CUDA: return "CUDA error";
+    case STENCIL_ERR_OOM: return "out of memory / workspace too small";
+    case STENCIL_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *stencil_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t stencil_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// run.cu -- stencil_run / stencil_run_host: the sweep schedule.
+//
+// A run of `steps` steps is ceil(steps / t) fused sweeps of depth t (the
+// last one shorter when t does not divide steps).  Sweep k reads the output
+// of sweep k-1 (the first reads `in`) and the buffers alternate between
+// `out` and the workspace so that the last sweep lands in `out`; `in` is
+// never written.  The fixed halo of `in` is copied once to every buffer
+// that a sweep writes, because sweeps only write interior points.
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+namespace gbs {
+
+namespace {
+
+template <typename T>
+__global__ void halo_copy_kernel(const T *__restrict__ in, T *__restrict__ out, T *__restrict__ out2, int64_t Ez,
+                                 int64_t Ey, int64_t Ex, int R, int zhalo)
+{
+    // one warp per stored row (z, y); halo rows are copied whole, interior
+    // rows only at their R cells on each end
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < Ez * Ey; row += warps) {
+        const int64_t z = row / Ey, y = row % Ey;
+        const bool halo_row = y < R || y >= Ey - R || (zhalo && (z < R || z >= Ez - R));
+        const int64_t base = row * Ex;
+        if (halo_row) {
+            for (int64_t x = lane; x < Ex; x += 32) {
+                T v = in[base + x];
+                out[base + x] = v;
+                if (out2) out2[base + x] = v;
+            }
+        } else {
+            for (int64_t i = lane; i < 2 * R; i += 32) {
+                const int64_t x = i < R ? i : Ex - 2 * R + i;
+                T v = in[base + x];
+                out[base + x] = v;
+                if (out2) out2[base + x] = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+stencil_status launch_halo_copy(const Plan &p, const void *in, void *out, void *out2, cudaStream_t st)
+{
+    const int R = p.pat.r;
+    const int64_t rows = p.ext[0] * p.ext[1];
+    int64_t blocks = (rows + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (p.dtype == STENCIL_F64)
+        halo_copy_kernel<double><<<(unsigned)blocks, 256, 0, st>>>((const double *)in, (double *)out,
+                                                                   (double *)out2, p.ext[0], p.ext[1], p.ext[2],
+                                                                   R, p.pat.d == 3);
+    else
+        halo_copy_kernel<float><<<(unsigned)blocks, 256, 0, st>>>((const float *)in, (float *)out, (float *)out2,
+                                                                  p.ext[0], p.ext[1], p.ext[2], R,
+                                                                  p.pat.d == 3);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "halo_copy launch");
+}
+
+static stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, size_t ws_bytes, int64_t steps,
+                                 cudaStream_t st)
+{
+    if (steps == 0) {
+        cudaError_t e = cudaMemcpyAsync(out, in, p.grid_bytes(), cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaMemcpyAsync(in -> out)");
+    }
+    const int t = p.t;
+    const int64_t nfull = steps / t;
+    const int rem = (int)(steps % t);
+    const int64_t nsweeps = nfull + (rem ? 1 : 0);
+    if (nsweeps > 1) {
+        if (!ws || ws_bytes < p.grid_bytes())
+            return fail(STENCIL_ERR_OOM, "stencil_run: more than one sweep needs a workspace of one grid "
+                                         "(stencil_plan_set_workspace)");
+        const char *a = (const char *)ws, *b = (const char *)in, *c = (const char *)out;
+        const size_t g = p.grid_bytes();
+        if ((a < b + g && b < a + g) || (a < c + g && c < a + g))
+            return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: workspace overlaps in or out");
+    }
+    stencil_status s = launch_halo_copy(p, in, out, nsweeps > 1 ? ws : nullptr, st);
+    if (s != STENCIL_OK) return s;
+    const void *src = in;
+    for (int64_t k = 0; k < nsweeps; k++) {
+        void *dst = ((nsweeps - 1 - k) % 2 == 0) ? out : ws;
+        const int tk = (k == nsweeps - 1 && rem) ? rem : t;
+        if (p.path == STENCIL_PATH_CUDA_CORE) {
+            s = launch_cu_sweep(p, src, dst, tk, st);
+        } else {
+            s = fail(STENCIL_ERR_UNSUPPORTED, "path not built");
+        }
+        if (s != STENCIL_OK) return s;
+        src = dst;
+    }
+    return STENCIL_OK;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_t steps,
+                                      stencil_stream_t stream)
+{
+    if (!plan || !in || !out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: null argument");
+    if (in == out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: in and out must differ");
+    if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: steps < 0");
+    Plan &p = plan->p;
+    {
+        const char *b = (const char *)in, *c = (const char *)out;
+        const size_t g = p.grid_bytes();
+        if (b < c + g && c < b + g) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: in and out overlap");
+    }
+    return run_sweeps(p, in, out, p.ws, p.ws_bytes, steps, (cudaStream_t)stream);
+}
+
+extern "C" stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out, int64_t steps,
+                                           stencil_stream_t stream)
+{
+    if (!plan || !host_in || !host_out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_host: null argument");
+    if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_host: steps < 0");
+    Plan &p = plan->p;
+    const size_t g = p.grid_bytes();
+    if (!p.ws || p.ws_bytes < 3 * g)
+        return fail(STENCIL_ERR_OOM, "stencil_run_host: needs a workspace of three grids");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *d_in = (char *)p.ws, *d_out = d_in + g, *d_ws = d_in + 2 * g;
+    cudaError_t e = cudaMemcpyAsync(d_in, host_in, g, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(host -> device)");
+    stencil_status s = run_sweeps(p, d_in, d_out, d_ws, g, steps, st);
+    if (s != STENCIL_OK) return s;
+    e = cudaMemcpyAsync(host_out, d_out, g, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(device -> host)");
+    e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaStreamSynchronize");
+}

@@ -13,7 +13,9 @@ FP64 sum, then the interior field in row-major order.  The halo is 0.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import math
+import os
 
 import numpy as np
 
@@ -38,12 +40,22 @@ def splitmix64(seed: int, start: int, count: int) -> np.ndarray:
 
 
 def uniform01(seed: int, start: int, count: int) -> np.ndarray:
-    """Doubles in (0, 1): ((x >> 11) + 0.5) * 2^-53."""
+    """Doubles in (0, 1): ((x >> 11) + 0.5) * 2^-53.  Large draws are split
+    over threads (each chunk is independent: the generator is counter-based)."""
     out = np.empty(count, dtype=np.float64)
-    for c0 in range(0, count, _CHUNK):
+
+    def fill(c0):
         n = min(_CHUNK, count - c0)
         x = splitmix64(seed, start + c0, n)
         out[c0:c0 + n] = ((x >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+
+    chunks = range(0, count, _CHUNK)
+    if count > 4 * _CHUNK:
+        with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, chunks))
+    else:
+        for c0 in chunks:
+            fill(c0)
     return out
 
 

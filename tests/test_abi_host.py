@@ -1,0 +1,194 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every function include/gbstencil.h declares, validates arguments, and its
+model (the dispatch rule) agrees with the oracle's copy of the paper's model.
+No test here launches a kernel."""
+import ctypes
+import itertools
+
+import pytest
+
+from oracle import model
+from paper_2603_00477_gb300 import binding as B
+from paper_2603_00477_gb300 import build as gbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return B.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = B.declared_symbols()
+    assert "stencil_plan_create" in names and "stencil_run" in names and "stencil_plan_destroy" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for s in range(6):
+        assert B.stencil_status_string(s)
+    assert B.stencil_status_string(0) == "ok"
+
+
+def _w(shape, d, r):
+    return [1.0 / model.K_points(shape, d, r)] * model.K_points(shape, d, r)
+
+
+@pytest.mark.parametrize("args,status", [
+    (("box", 1, 1, "f64", (8,)), B.STENCIL_ERR_INVALID_ARG),        # d = 1
+    (("box", 4, 1, "f64", (8, 8, 8, 8)), B.STENCIL_ERR_INVALID_ARG),  # d = 4
+    (("box", 2, 0, "f64", (8, 8)), B.STENCIL_ERR_INVALID_ARG),      # r = 0
+    (("box", 2, 1, "f64", (0, 8)), B.STENCIL_ERR_INVALID_ARG),      # empty extent
+    (("box", 2, 1, "f64", (-3, 8)), B.STENCIL_ERR_INVALID_ARG),
+    (("box", 3, 3, "f64", (8, 8, 8)), B.STENCIL_ERR_UNSUPPORTED),   # no 3-D box r=3 kernel
+    (("box", 2, 9, "f32", (64, 64)), B.STENCIL_ERR_UNSUPPORTED),
+])
+def test_plan_create_rejects(lib, args, status):
+    shape, d, r, dt, dims = args
+    K = model.K_points(shape, max(d, 1), max(r, 1)) if 1 <= d <= 3 else 1
+    with pytest.raises(B.StencilError) as e:
+        B.stencil_plan_create(shape, d, r, [0.1] * K, dt, dims, 0)
+    assert e.value.status == status
+
+
+def test_plan_create_rejects_nonfinite_and_bad_t(lib):
+    w = _w("box", 2, 1)
+    w[3] = float("nan")
+    with pytest.raises(B.StencilError):
+        B.stencil_plan_create("box", 2, 1, w, "f64", (8, 8), 0)
+    with pytest.raises(B.StencilError):
+        B.stencil_plan_create("box", 2, 1, _w("box", 2, 1), "f64", (8, 8), 17)
+
+
+def test_null_pointer_arguments(lib):
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 2)(8, 8)
+    assert lib.stencil_plan_create(None, 0, 2, 1, (ctypes.c_double * 9)(), 0, dims, 0) == B.STENCIL_ERR_INVALID_ARG
+    assert lib.stencil_plan_create(ctypes.byref(h), 0, 2, 1, None, 0, dims, 0) == B.STENCIL_ERR_INVALID_ARG
+    assert lib.stencil_run(None, None, None, 1, None) == B.STENCIL_ERR_INVALID_ARG
+    assert lib.stencil_plan_info(None, None) == B.STENCIL_ERR_INVALID_ARG
+    lib.stencil_plan_destroy(None)
+
+
+def test_run_argument_checks_launch_nothing(lib):
+    p = B.stencil_plan_create("box", 2, 1, _w("box", 2, 1), "f64", (8, 8), 1)
+    try:
+        n0 = B.stencil_launch_count()
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_run(p, 4096, 4096, 3, 0)  # in == out
+        assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_run(p, 4096, 1 << 20, -1, 0)
+        assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        with pytest.raises(B.StencilError) as e:  # overlapping buffers
+            B.stencil_run(p, 4096, 4096 + 8, 3, 0)
+        assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        with pytest.raises(B.StencilError) as e:  # > 1 sweep without workspace
+            B.stencil_run(p, 4096, 1 << 20, 3, 0)
+        assert e.value.status == B.STENCIL_ERR_OOM
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_run_host(p, 4096, 1 << 20, 1, 0)
+        assert e.value.status == B.STENCIL_ERR_OOM
+        assert B.stencil_launch_count() == n0
+    finally:
+        B.stencil_plan_destroy(p)
+
+
+def test_workspace_bytes(lib):
+    p = B.stencil_plan_create("star", 3, 2, _w("star", 3, 2), "f32", (5, 6, 7), 1)
+    try:
+        g = 9 * 10 * 11 * 4
+        assert B.stencil_plan_workspace_bytes(p) == g
+        assert B.stencil_plan_workspace_bytes(p, True) == 3 * g
+    finally:
+        B.stencil_plan_destroy(p)
+
+
+def test_options(lib):
+    p = B.stencil_plan_create("box", 2, 2, _w("box", 2, 2), "f32", (100, 200), 0)
+    try:
+        B.stencil_plan_set_option(p, "t", "3")
+        assert B.stencil_plan_info(p)["t"] == 3
+        B.stencil_plan_set_option(p, "tile", "32x64")
+        assert B.stencil_plan_info(p)["tile"] == [1, 32, 64]
+        B.stencil_plan_set_option(p, "path", "cuda_core")
+        for k, v in (("nope", "1"), ("t", "99"), ("path", "fpga"), ("tile", "3x5x7"), ("precision", "fp8")):
+            with pytest.raises(B.StencilError) as e:
+                B.stencil_plan_set_option(p, k, v)
+            assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        assert B.stencil_plan_info(p)["t"] == 3  # failed options leave the plan unchanged
+    finally:
+        B.stencil_plan_destroy(p)
+
+
+def test_fp64_rejects_reduced_precision(lib):
+    p = B.stencil_plan_create("box", 2, 3, _w("box", 2, 3), "f64", (64, 64), 0)
+    try:
+        with pytest.raises(B.StencilError):
+            B.stencil_plan_set_option(p, "precision", "tf32")
+    finally:
+        B.stencil_plan_destroy(p)
+
+
+# ---- the product's model against the oracle's ---------------------------------------
+
+@pytest.mark.parametrize("shape,d,r,t,D,S,beta", list(itertools.product(
+    ("box", "star"), (2, 3), (1, 2, 3), (1, 2, 4, 7), (4, 8), (0.3125, 0.5, 1.0), (1.0, 3.0)))[::7])
+def test_model_matches_oracle_model(lib, shape, d, r, t, D, S, beta):
+    P_cu, P_tc, Bw = 80e12, 1.1e15, 6.8e12
+    got = B.stencil_model_predict(shape, d, r, t, D, S, beta, P_cu, P_tc, Bw)
+    assert got["K"] == model.K_points(shape, d, r)
+    assert got["K_fused"] == model.K_fused(shape, d, r, t)
+    assert got["alpha"] == pytest.approx(model.alpha(shape, d, r, t), rel=1e-14)
+    assert got["I_cu"] == pytest.approx(model.I_cu(shape, d, r, t, D), rel=1e-14)
+    assert got["I_tc"] == pytest.approx(model.I_tc(shape, d, r, t, D, S, beta), rel=1e-14)
+    assert got["C_tc"] == pytest.approx(model.C_tc(shape, d, r, t, S, beta), rel=1e-14)
+    assert got["P_tc_actual"] == pytest.approx(model.P_tc_actual(shape, d, r, t, D, S, P_tc, Bw, beta), rel=1e-14)
+    assert got["P_cu_actual"] == pytest.approx(model.P_cu_actual(shape, d, r, t, D, P_cu, Bw), rel=1e-14)
+    assert got["scenario"] == model.scenario(shape, d, r, t, D, S, P_cu, P_tc, Bw, beta)
+    assert bool(got["sweet_spot"]) == model.in_sweet_spot(shape, d, r, t, D, S, P_cu, P_tc, Bw, beta)
+    assert got["gstencils_cu"] * 1e9 == pytest.approx(model.gstencils_roof_cu(shape, d, r, t, D, P_cu, Bw))
+
+
+def test_model_rejects_bad_input(lib):
+    for bad in (dict(sparsity=0.0), dict(sparsity=1.5), dict(t=0), dict(B=0.0), dict(beta=0.5)):
+        args = dict(shape="box", d=2, r=1, t=1, dtype_bytes=8, sparsity=0.5, beta=1.0, P_cu=1e12, P_tc=2e12, B=1e12)
+        args.update(bad)
+        with pytest.raises(B.StencilError):
+            B.stencil_model_predict(**args)
+
+
+def test_peaks_roundtrip(lib):
+    old = B.stencil_get_peaks()
+    try:
+        B.stencil_set_peaks(hbm_bytes_per_s=1.0e12)
+        assert B.stencil_get_peaks()["hbm_bytes_per_s"] == 1.0e12
+        assert B.stencil_get_peaks()["cu_f64_flops"] == old["cu_f64_flops"]  # zero fields unchanged
+    finally:
+        B.stencil_set_peaks(**old)
+
+
+def test_dispatch_fp64_picks_cuda_cores_t1(lib):
+    """With GB300's FP64 rate every FP64 configuration is compute-bound at
+    t=1 (ridge ~0.19 FLOP/B), so fusion cannot help and the CUDA-core t=1
+    plan is the fastest (ties go to CUDA cores and smaller t)."""
+    p = B.stencil_plan_create("box", 2, 3, _w("box", 2, 3), "f64", (16384, 16384), 0)
+    try:
+        info = B.stencil_plan_info(p)
+        assert info["path"] == B.PATH_CUDA_CORE and info["t"] == 1
+        assert info["memory_bound"] == 0
+        assert info["intensity"] == pytest.approx(49 / 8)
+    finally:
+        B.stencil_plan_destroy(p)
+
+
+def test_dispatch_fp32_fuses_until_compute_bound(lib):
+    """Box-2D2R FP32: I = 6.25 t against a CU ridge near 11.8 -> memory-bound at
+    t = 1, compute-bound from t = 2: the model picks t >= 2 on CUDA cores."""
+    p = B.stencil_plan_create("box", 2, 2, _w("box", 2, 2), "f32", (16384, 16384), 0)
+    try:
+        info = B.stencil_plan_info(p)
+        assert info["path"] == B.PATH_CUDA_CORE and info["t"] >= 2
+    finally:
+        B.stencil_plan_destroy(p)

@@ -109,8 +109,8 @@ def test_case1_degradation_matches_text():
 
 
 def test_scenario_identities():
-    """Scenario 1 ratio = 1 (Eq. 13); scenario 2 < 1 (Eq. 14); scenario 3 > 1
-    (Eq. 15); scenario 4 = (S/alpha) P_TC/P_CU (Eq. 16)."""
+    """Scenario 1 ratio = 1 (Eq. 14); scenario 2 < 1 (Eq. 16); scenario 3 > 1
+    (Eq. 17); scenario 4 = (S/alpha) P_TC/P_CU (Eq. 18)."""
     B = 1e12
     # S1: both memory-bound
     assert model.scenario("box", 2, 1, 1, 8, 0.5, 1e15, 1e16, B) == 1
