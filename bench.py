@@ -146,30 +146,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------
-def cpu_baseline(cfg, budget_s=15.0):
+def cpu_baseline(cfg, w, u, budget_s=15.0):
     """The oracle (as it stands) on a bounded sample of the workload: the same
-    stencil and dtype on a smaller grid, steps chosen for ~budget_s of CPU time."""
+    grid and initial field, but only as many of its steps as take about
+    budget_s of CPU time (at least one)."""
     import numpy as np
 
     import oracle
-    from paper_2603_00477_gb300 import inputs
+    u64 = np.ascontiguousarray(u, dtype=np.float64)
     d = cfg["d"]
-    side = 1024 if d == 2 else 96
-    dims = (side,) * d
-    npdt = np.float64 if cfg["dtype"] == "f64" else np.float32
-    w, u = inputs.problem(cfg["shape"], d, cfg["r"], dims, seed=cfg["seed"], dtype=npdt)
-    u = u.astype(np.float64)
+    probe_dims = (256,) * d if d == 2 else (48,) * d
+    small = np.ascontiguousarray(u64[tuple(slice(0, n + 2 * cfg["r"]) for n in probe_dims)])
     t0 = time.perf_counter()
-    oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, 1)
-    one = time.perf_counter() - t0
-    steps = max(1, min(cfg["steps"], int(budget_s / max(one, 1e-6))))
+    oracle.run(cfg["shape"], d, cfg["r"], w, probe_dims, small, 1)
+    per_point = (time.perf_counter() - t0) / math.prod(probe_dims)
+    steps = max(1, min(cfg["steps"], int(budget_s / max(per_point * points_of(cfg), 1e-9))))
     t0 = time.perf_counter()
-    oracle.run(cfg["shape"], d, cfg["r"], w, dims, u, steps)
+    oracle.run(cfg["shape"], d, cfg["r"], w, cfg["dims"], u64, steps)
     el = time.perf_counter() - t0
-    return {"value": math.prod(dims) * steps / el / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
+    return {"value": points_of(cfg) * steps / el / 1e9, "unit": UNIT, "cores": oracle.max_threads(),
             "kind": "oracle",
-            "sample": f"{cfg['shape']}-{d}D{cfg['r']}R {cfg['dtype']} on a {'x'.join(map(str, dims))} interior, "
-                      f"{steps} steps, FP64 C oracle with OpenMP ({el:.1f} s)"}
+            "sample": f"the full {'x'.join(map(str, cfg['dims']))} grid for {steps} of its {cfg['steps']} steps, "
+                      f"FP64 C oracle with OpenMP ({el:.1f} s)"}
 
 
 def run_reference(args, cfg, name, rank):
@@ -244,12 +242,18 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-(path, t) sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dims", default=None, help="override the interior extents (profiling), e.g. 6144,6144")
+    ap.add_argument("--run-steps", type=int, default=None, help="override the steps per run (profiling)")
     args = ap.parse_args()
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local_rank = _env_int("LOCAL_RANK", 0)
-    cfg = WORKLOADS[args.config]
+    cfg = dict(WORKLOADS[args.config])
+    if args.dims:
+        cfg["dims"] = tuple(int(x) for x in args.dims.split(","))
+    if args.run_steps:
+        cfg["steps"] = args.run_steps
     if args.impl == "reference":
         return run_reference(args, cfg, args.config, rank)
 
@@ -273,16 +277,15 @@ def main():
         if world > 1:
             dist.barrier()
 
-    # cpu baseline first (no GPU work yet in this process)
+    npdt = np.float64 if cfg["dtype"] == "f64" else np.float32
+    w, u = inputs.problem(cfg["shape"], cfg["d"], cfg["r"], cfg["dims"], seed=cfg["seed"], dtype=npdt,
+                          field=cfg.get("field", "uniform"))
+    # CPU baseline (the oracle, no process pool, before any GPU work here)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        cpu = cpu_baseline(cfg)
-
-    npdt = np.float64 if cfg["dtype"] == "f64" else np.float32
-    w, u = inputs.problem(cfg["shape"], cfg["d"], cfg["r"], cfg["dims"], seed=cfg["seed"], dtype=npdt,
-                          field=cfg.get("field", "uniform"))
+        cpu = cpu_baseline(cfg, w, u)
     plan = B.Plan(cfg["shape"], cfg["d"], cfg["r"], w, cfg["dtype"], cfg["dims"], args.t)
     if args.path != "auto":
         plan.set_option("path", args.path)
@@ -345,6 +348,11 @@ def main():
                 "peak_source": f"derived: 152 SMs x 2070 MHz x {'4' if D == 8 else '256'} FLOP/clk/SM "
                                f"({cfg['dtype'].upper()} FMA pipe)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof["bound"] == "alu":
+        probe = B.stencil_probe_peaks(stream)
+        measured = probe["cu_f64_flops" if D == 8 else "cu_f32_flops"] / 1e12
+        roof["probe_peak"] = measured
+        roof["probe_frac"] = roof["achieved"] / measured
     roof["traffic"] = traffic
     roof["kernel"] = kernel_key
     roof["avg_launch_ms"] = avg_launch_s * 1e3

@@ -137,6 +137,21 @@ typedef struct {
     double gstencils_cu, gstencils_tc; /* point-updates/s / 1e9 at the roofs */
 } stencil_model_out;
 
+/* Geometry of the tensor-core Toeplitz operands for one fusion depth
+ * (paper Sec. 2.2: the stencil recast as an MMA over zero-padded banded
+ * matrices).  For line a (row a of the composite kernel w^(t), a = -R..R)
+ * the B operand is B_a[k][n] = w^(t)[a][k - n - R] for |k - n - R| <= R,
+ * else 0, k in [0, kext), n in [0, n_tile); the MMAs issue the K blocks
+ * kb_lo[a]..kb_hi[a] of k_inst columns each. */
+typedef struct {
+    int R;          /* fused radius t*r                          */
+    int n_tile;     /* MMA N: output columns per accumulator     */
+    int k_inst;     /* MMA K per instruction                     */
+    int kext;       /* padded K extent of one line               */
+    int nkb;        /* kext / k_inst                             */
+    double sparsity;/* S = useful MACs / issued MACs             */
+} stencil_tc_layout;
+
 typedef struct stencil_plan stencil_plan;
 
 /* ---- plans ------------------------------------------------------------- */
@@ -191,6 +206,14 @@ stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_
 stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out,
                                 int64_t steps, stencil_stream_t stream);
 
+/* The tensor-core operand layout of this plan's (dtype, precision) at fusion
+ * depth t (host only).  kb_lo/kb_hi receive 2R+1 ints each; B (optional)
+ * receives the FP64 Toeplitz blocks in [a][kb][k][n] order,
+ * (2R+1) * nkb * k_inst * n_tile doubles.  Any of kb_lo, kb_hi, B may be null.
+ * UNSUPPORTED when the tensor-core path has no kernel for the plan at this t. */
+stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_tc_layout *layout, int *kb_lo,
+                                      int *kb_hi, double *B);
+
 /* Release a plan (never frees caller workspace).  Null is ignored. */
 void stencil_plan_destroy(stencil_plan *plan);
 
@@ -208,12 +231,24 @@ stencil_status stencil_model_predict(const stencil_model_in *in, stencil_model_o
 stencil_status stencil_set_peaks(const stencil_peaks *peaks);
 stencil_status stencil_get_peaks(stencil_peaks *peaks);
 
+/* Measure the FP64 and FP32 FMA-pipe rates of the current device (FLOP/s,
+ * independent FMA chains in registers, timed with CUDA events on `stream`;
+ * synchronises `stream`).  Fills cu_f64_flops and cu_f32_flops, zeroes the
+ * other fields; does not change the dispatcher's table.  Takes about a
+ * second. */
+stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_stream_t stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
+
+/* Synchronise `stream` and report whether a tensor-core kernel gave up a
+ * bounded wait for its MMAs since the last call (STENCIL_ERR_TIMEOUT; the
+ * affected outputs were not written).  Clears the flag. */
+stencil_status stencil_device_status(stencil_stream_t stream);
 
 const char *stencil_status_string(stencil_status s);
 const char *stencil_last_error(void);
-/* Kernel launches the calling thread has issued through this library since
- * the process started (counted on the host at each launch). */
+/* Kernel launches issued through this library since it was loaded, by all
+ * threads (counted on the host at each launch). */
 uint64_t stencil_launch_count(void);
 
 #ifdef __cplusplus

@@ -47,6 +47,11 @@ class stencil_info(ctypes.Structure):
                 ("predicted_cu_gstencils", ctypes.c_double), ("predicted_tc_gstencils", ctypes.c_double)]
 
 
+class stencil_tc_layout(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int), ("n_tile", ctypes.c_int), ("k_inst", ctypes.c_int), ("kext", ctypes.c_int),
+                ("nkb", ctypes.c_int), ("sparsity", ctypes.c_double)]
+
+
 class stencil_model_in(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("d", ctypes.c_int), ("r", ctypes.c_int), ("t", ctypes.c_int),
                 ("dtype_bytes", ctypes.c_int), ("sparsity", ctypes.c_double), ("beta", ctypes.c_double),
@@ -100,6 +105,14 @@ def load() -> ctypes.CDLL:
     L.stencil_set_peaks.restype = st
     L.stencil_get_peaks.argtypes = [ctypes.POINTER(stencil_peaks)]
     L.stencil_get_peaks.restype = st
+    L.stencil_probe_peaks.argtypes = [ctypes.POINTER(stencil_peaks), vp]
+    L.stencil_probe_peaks.restype = st
+    L.stencil_plan_tc_layout.argtypes = [vp, ctypes.c_int, ctypes.POINTER(stencil_tc_layout),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_double)]
+    L.stencil_plan_tc_layout.restype = st
+    L.stencil_device_status.argtypes = [vp]
+    L.stencil_device_status.restype = st
     L.stencil_status_string.argtypes = [ctypes.c_int]
     L.stencil_status_string.restype = ctypes.c_char_p
     L.stencil_last_error.argtypes = []
@@ -182,6 +195,26 @@ def stencil_run_host(plan: int, host_in_ptr: int, host_out_ptr: int, steps: int,
            "stencil_run_host")
 
 
+def stencil_plan_tc_layout(plan: int, t: int, with_B: bool = True):
+    """(layout dict, kb_lo list, kb_hi list, B array [a][kb][k][n] or None)."""
+    import numpy as np
+    lay = stencil_tc_layout()
+    _check(load().stencil_plan_tc_layout(plan, int(t), ctypes.byref(lay), None, None, None), "stencil_plan_tc_layout")
+    lines = 2 * lay.R + 1
+    lo = (ctypes.c_int * lines)()
+    hi = (ctypes.c_int * lines)()
+    B = np.zeros((lines, lay.nkb, lay.k_inst, lay.n_tile), dtype=np.float64) if with_B else None
+    _check(load().stencil_plan_tc_layout(plan, int(t), ctypes.byref(lay), lo, hi,
+                                         B.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if with_B else None),
+           "stencil_plan_tc_layout")
+    d = {f: getattr(lay, f) for f, _ in stencil_tc_layout._fields_}
+    return d, list(lo), list(hi), B
+
+
+def stencil_device_status(stream=None) -> None:
+    _check(load().stencil_device_status(_stream_handle(stream)), "stencil_device_status")
+
+
 def stencil_plan_destroy(plan: int) -> None:
     if plan:
         load().stencil_plan_destroy(plan)
@@ -202,6 +235,12 @@ def stencil_set_peaks(**kw) -> None:
 def stencil_get_peaks() -> dict:
     p = stencil_peaks()
     _check(load().stencil_get_peaks(ctypes.byref(p)), "stencil_get_peaks")
+    return {f: getattr(p, f) for f, _ in stencil_peaks._fields_}
+
+
+def stencil_probe_peaks(stream=None) -> dict:
+    p = stencil_peaks()
+    _check(load().stencil_probe_peaks(ctypes.byref(p), _stream_handle(stream)), "stencil_probe_peaks")
     return {f: getattr(p, f) for f, _ in stencil_peaks._fields_}
 
 

@@ -67,17 +67,48 @@ struct Weights {
 // ---------------------------------------------------------------------------
 // 2-D: tile BY x BX, strips of V rows.
 // ---------------------------------------------------------------------------
+// Band mode (band > 0): only the tiles of the ring of tile rows/columns that
+// touch the band run (a 1-D grid, ring.count blocks), and only points closer
+// than `band` to the interior boundary are written.  Used after a
+// tensor-core sweep, whose fused kernel is exact only away from the
+// boundary.
+struct Ring {
+    int band;        // 0: whole grid (2-D launch grid)
+    int nty, ntx;    // tiles along y and x
+    int rows_tb;     // tile rows taken whole (top + bottom)
+    int by_w;        // top ring rows
+    int cols_lr;     // tile columns taken in the middle rows (left + right)
+    int bx_w;        // left ring columns
+};
+
+__device__ __forceinline__ void ring_tile(const Ring &g, int id, int *by, int *bx)
+{
+    if (id < g.rows_tb * g.ntx) {
+        const int rr = id / g.ntx;
+        *bx = id % g.ntx;
+        *by = rr < g.by_w ? rr : g.nty - g.rows_tb + rr;
+    } else {
+        const int id2 = id - g.rows_tb * g.ntx;
+        const int cc = id2 % g.cols_lr;
+        *by = g.by_w + id2 / g.cols_lr;
+        *bx = cc < g.bx_w ? cc : g.ntx - g.cols_lr + cc;
+    }
+}
+
 template <typename T, int SHAPE, int R, int V>
 __global__ void __launch_bounds__(kThreads)
     cu2d_sweep(const T *__restrict__ in, T *__restrict__ out, const Weights<T, Taps<SHAPE, 2, R>::K> wt,
-               int64_t Ey, int64_t Ex, int BY, int BX, int t)
+               int64_t Ey, int64_t Ex, int BY, int BX, int t, const Ring ring)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int H = BY + 2 * t * R, W = BX + 2 * t * R;
     T *bufA = reinterpret_cast<T *>(smem_raw);
     T *bufB = bufA + (size_t)H * W;
-    const int64_t Y0 = R + (int64_t)blockIdx.y * BY - (int64_t)t * R;
-    const int64_t X0 = R + (int64_t)blockIdx.x * BX - (int64_t)t * R;
+    int tby = blockIdx.y, tbx = blockIdx.x;
+    if (ring.band > 0) ring_tile(ring, blockIdx.x, &tby, &tbx);
+    const int64_t Y0 = R + (int64_t)tby * BY - (int64_t)t * R;
+    const int64_t X0 = R + (int64_t)tbx * BX - (int64_t)t * R;
+    const int64_t ny = Ey - 2 * R, nx = Ex - 2 * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
     // Stage the dependency region; cells outside the stored array read 0
@@ -136,7 +167,13 @@ __global__ void __launch_bounds__(kThreads)
                     const int64_t gy = Y0 + y;
                     const bool interior = colint && gy >= R && gy < Ey - R;
                     if (last) {
-                        if (interior) out[gy * Ex + gx] = acc[j];
+                        bool keep = interior;
+                        if (ring.band > 0) {
+                            const int64_t iy = gy - R, ix = gx - R;
+                            keep = keep && (iy < ring.band || ix < ring.band || ny - 1 - iy < ring.band ||
+                                            nx - 1 - ix < ring.band);
+                        }
+                        if (keep) out[gy * Ex + gx] = acc[j];
                     } else {
                         dst[y * W + x] = interior ? acc[j] : src[y * W + x];
                     }

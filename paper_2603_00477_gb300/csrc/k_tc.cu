@@ -1,0 +1,457 @@
+// k_tc.cu -- tensor-core sweeps: the t-step composite stencil (kernel fusion,
+// paper Sec. 2.2.3, Eq. 3) run as banded Toeplitz GEMM tiles.
+//
+// FP32 grids (tc2d_sweep): tcgen05.mma with D in TMEM.  A CTA owns 128
+// output rows x 8*NACC output columns; the MMA M axis runs over the 128
+// rows, N = 8 output columns per accumulator, K over the input window.  The
+// input tile sits in shared memory "chunk-column major": 16-byte chunks of
+// consecutive x, with the 16-byte chunks of consecutive rows adjacent.  Any
+// 8 consecutive rows of one chunk column therefore form a canonical K-major
+// core matrix, so the im2col operand A_a of line a is only a descriptor:
+// start = chunk column of the window, row offset a; LBO = one chunk column
+// (HS * 16 bytes), SBO = 8 rows (128 bytes).  No copy is made.  B_a is the
+// Toeplitz block of line a, built in shared memory by the CTA from the
+// composite weights.  One thread issues all MMAs of the tile, commits them to
+// an mbarrier; the four warps then read the accumulators back with
+// tcgen05.ld, stage them through shared memory and store coalesced rows.
+//
+// Precision forms: TF32 (one product of TF32-rounded operands), TF32X3 and
+// BF16X3 (each operand split into hi + lo, three products hi*hi + hi*lo +
+// lo*hi accumulated in FP32).
+//
+// FP64 grids (dmma2d_sweep): the same Toeplitz formulation on the FP64 MMA
+// mma.sync.m8n8k4 (M = 8 output rows, N = 8 output columns, K = 4).
+//
+// Both write interior points farther than (t-1) r from the boundary only:
+// nearer points would need the halo re-imposed between the fused steps; the
+// CUDA-core band kernel computes them stepwise.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cu_kernels.cuh"
+#include "launch.h"
+#include "tc_layout.h"
+#include "tc_ptx.cuh"
+
+namespace gbs {
+
+constexpr int kTcMaxR = 12;
+constexpr int kTcMaxLines = 2 * kTcMaxR + 1;
+
+struct TcParams {
+    double w[kTcMaxLines * kTcMaxLines];  // composite w^(t), (2R+1) x (2R+1), row-major
+    unsigned char kb_lo[kTcMaxLines], kb_hi[kTcMaxLines];
+    int R, rh, band, nkb, hs, nch;
+    int64_t Ey, Ex;
+};
+
+__device__ int g_tc_error;
+
+namespace tcs {
+
+using namespace tc;
+
+constexpr int TM = 128;
+constexpr int TN = 8;
+enum { P_TF32 = 0, P_TF32X3 = 1, P_BF16X3 = 2 };
+
+template <int PREC>
+struct Elem;
+template <>
+struct Elem<P_TF32> {
+    static constexpr int bytes = 4;
+};
+template <>
+struct Elem<P_TF32X3> {
+    static constexpr int bytes = 4;
+};
+template <>
+struct Elem<P_BF16X3> {
+    static constexpr int bytes = 2;
+};
+
+template <int PREC>
+__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, float v)
+{
+    if (PREC == P_BF16X3) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        *reinterpret_cast<__nv_bfloat16 *>(hi) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(lo) = l;
+    } else if (PREC == P_TF32X3) {
+        float h = to_tf32(v);
+        *reinterpret_cast<float *>(hi) = h;
+        *reinterpret_cast<float *>(lo) = to_tf32(v - h);
+    } else {
+        *reinterpret_cast<float *>(hi) = to_tf32(v);
+    }
+}
+
+// hi/lo split of a weight given in FP64: hi = round(w), lo = round(w - hi).
+template <int PREC>
+__device__ __forceinline__ void split_store_w(unsigned char *hi, unsigned char *lo, double w)
+{
+    if (PREC == P_BF16X3) {
+        __nv_bfloat16 h = __float2bfloat16_rn((float)w);
+        __nv_bfloat16 l = __float2bfloat16_rn((float)(w - (double)__bfloat162float(h)));
+        *reinterpret_cast<__nv_bfloat16 *>(hi) = h;
+        *reinterpret_cast<__nv_bfloat16 *>(lo) = l;
+    } else if (PREC == P_TF32X3) {
+        float h = to_tf32((float)w);
+        *reinterpret_cast<float *>(hi) = h;
+        *reinterpret_cast<float *>(lo) = to_tf32((float)(w - (double)h));
+    } else {
+        *reinterpret_cast<float *>(hi) = to_tf32((float)w);
+    }
+}
+
+__device__ __forceinline__ bool outside_band(int64_t iy, int64_t ix, int64_t ny, int64_t nx, int band)
+{
+    return iy >= band && ix >= band && ny - 1 - iy >= band && nx - 1 - ix >= band;
+}
+
+constexpr unsigned long long kWaitCycles = 4ull << 30;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ bool wait_mbar_cycles(uint64_t *mbar, uint32_t phase)
+{
+    const unsigned long long t0 = clock64();
+    while (!mbar_try_wait(mbar, phase)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+template <int PREC, int NACC>
+__global__ void __launch_bounds__(128) tc2d_sweep(const float *__restrict__ in, float *__restrict__ out,
+                                                  const __grid_constant__ TcParams p)
+{
+    constexpr bool SPLIT = PREC != P_TF32;
+    constexpr int ES = Elem<PREC>::bytes;
+    constexpr int E = 16 / ES;  // elements per 16-byte chunk
+    constexpr int KI = 2 * E;   // MMA K per instruction (32 bytes of K)
+    constexpr int TX = NACC * TN;
+    constexpr int SP = TX + 4;  // staging row pitch (floats)
+    constexpr uint32_t kCols = NACC * TN;
+    static_assert(kCols >= 32 && (kCols & (kCols - 1)) == 0, "TMEM columns: power of two >= 32");
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int R = p.R, HS = p.hs, NCH = p.nch, nkb = p.nkb;
+    const int lines = 2 * R + 1;
+    const uint32_t a_bytes = (uint32_t)NCH * HS * 16;
+    const uint32_t b_bytes = (uint32_t)lines * nkb * 256;
+    // [0,16): TMEM address + mbarrier; operands from byte 128
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 8);
+    unsigned char *A0 = smem + 128;
+    unsigned char *A1 = A0 + (SPLIT ? a_bytes : 0);
+    unsigned char *B0 = A0 + a_bytes * (SPLIT ? 2 : 1);
+    unsigned char *B1 = B0 + (SPLIT ? b_bytes : 0);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t Y0 = p.rh + (int64_t)blockIdx.y * TM;  // stored row of output row 0
+    const int64_t X0 = p.rh + (int64_t)blockIdx.x * TX;  // stored column of output column 0
+    const int64_t ny = p.Ey - 2 * p.rh, nx = p.Ex - 2 * p.rh;
+
+    if (warp == 0) tmem_alloc(tmem_slot, kCols);
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+    }
+
+    // Toeplitz blocks: block (line a, k-block kb) holds B_a[kb*KI + k][n] for
+    // n < 8, k < KI as two core matrices (k chunks) of 8 rows (n) x 16 bytes.
+    const int bent = lines * nkb * 8 * KI;
+    for (int idx = tid; idx < bent; idx += blockDim.x) {
+        const int k = idx % KI;
+        const int n = (idx / KI) % 8;
+        const int blk = idx / (8 * KI);  // = ai * nkb + kb
+        const int ai = blk / nkb, kb = blk % nkb;
+        const int b = kb * KI + k - n - R;
+        const double wv = (b >= -R && b <= R) ? p.w[ai * lines + (b + R)] : 0.0;
+        const uint32_t off = blk * 256 + (k / E) * 128 + n * 16 + (k % E) * ES;
+        split_store_w<PREC>(B0 + off, B1 + off, wv);
+    }
+    // Input tile: rows Y0-R .. Y0+TM+R-1, columns X0-R .. X0-R+NCH*E-1.
+    const int rows = TM + 2 * R, cols = NCH * E;
+    for (int row = warp; row < rows; row += 4) {
+        const int64_t gy = Y0 - R + row;
+        const bool rowok = gy >= 0 && gy < p.Ey;
+        const float *src = in + gy * p.Ex;
+        for (int x = lane; x < cols; x += 32) {
+            const int64_t gx = X0 - R + x;
+            const float v = (rowok && gx >= 0 && gx < p.Ex) ? __ldg(src + gx) : 0.0f;
+            const uint32_t off = (uint32_t)(x / E) * HS * 16 + row * 16 + (x % E) * ES;
+            split_store<PREC>(A0 + off, A1 + off, v);
+        }
+    }
+    fence_proxy_async_smem();
+    fence_before_thread_sync();
+    __syncthreads();
+    fence_after_thread_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (tid == 0) {
+        const uint32_t idesc = instr_desc(PREC == P_BF16X3 ? kFmtBF16 : kFmtTF32, TM, TN);
+        const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1), b0 = smem_u32(B0), b1 = smem_u32(B1);
+        const uint32_t lbo_a = (uint32_t)HS * 16;
+        for (int q = 0; q < NACC; ++q) {
+            uint32_t acc = 0;
+            const uint32_t d = tmem + q * TN;
+            for (int ai = 0; ai < lines; ++ai) {
+                for (int kb = p.kb_lo[ai]; kb <= p.kb_hi[ai]; ++kb) {
+                    const uint32_t aoff = (uint32_t)(q * (TN / E) + 2 * kb) * lbo_a + ai * 16;
+                    const uint32_t boff = (uint32_t)(ai * nkb + kb) * 256;
+                    const uint64_t da0 = smem_desc(a0 + aoff, lbo_a, 128);
+                    const uint64_t db0 = smem_desc(b0 + boff, 128, 256);
+                    if (PREC == P_BF16X3) {
+                        mma_f16(d, da0, db0, idesc, acc);
+                        mma_f16(d, da0, smem_desc(b1 + boff, 128, 256), idesc, 1);
+                        mma_f16(d, smem_desc(a1 + aoff, lbo_a, 128), db0, idesc, 1);
+                    } else {
+                        mma_tf32(d, da0, db0, idesc, acc);
+                        if (SPLIT) {
+                            mma_tf32(d, da0, smem_desc(b1 + boff, 128, 256), idesc, 1);
+                            mma_tf32(d, smem_desc(a1 + aoff, lbo_a, 128), db0, idesc, 1);
+                        }
+                    }
+                    acc = 1;
+                }
+            }
+        }
+        mma_commit(mbar);
+    }
+    __syncwarp();
+    const bool ok = wait_mbar_cycles(mbar, 0);
+    fence_after_thread_sync();
+    if (!ok) {
+        atomicExch(&g_tc_error, 1);
+        wait_mbar_cycles(mbar, 0);  // give in-flight MMAs a second chance before freeing TMEM
+    }
+    __syncthreads();  // every thread has seen the MMAs complete before the operands are reused
+    if (ok) {
+        // TMEM -> registers -> staging (reuses the operand area: the MMAs are done)
+        float *stage = reinterpret_cast<float *>(A0);
+        const int m = warp * 32 + lane;
+        for (int q = 0; q < NACC; ++q) {
+            uint32_t v[8];
+            tmem_ld_32x32b_x8(tmem + ((uint32_t)(warp * 32) << 16) + q * TN, v);
+            tmem_ld_wait();
+            float4 *dst = reinterpret_cast<float4 *>(stage + m * SP + q * TN);
+            dst[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                 __uint_as_float(v[3]));
+            dst[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]),
+                                 __uint_as_float(v[7]));
+        }
+        __syncthreads();
+        for (int row = warp; row < TM; row += 4) {
+            const int64_t gy = Y0 + row;
+            const int64_t iy = gy - p.rh;
+            if (iy >= ny) break;
+            float *dstrow = out + gy * p.Ex;
+            for (int x = lane; x < TX; x += 32) {
+                const int64_t ix = X0 + x - p.rh;
+                if (ix < nx && outside_band(iy, ix, ny, nx, p.band)) dstrow[X0 + x] = stage[row * SP + x];
+            }
+        }
+    }
+    fence_before_thread_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// ---------------------------------------------------------------------------
+// FP64: mma.sync.m8n8k4 (A 8x4 row-major, B 4x8 column-major, C/D 8x8).
+// 256 threads; a CTA owns 64 output rows x 64 output columns; warp w owns
+// rows 8w..8w+7 and eight 8-column accumulators.
+// ---------------------------------------------------------------------------
+constexpr int DM_T = 64;
+
+__device__ __forceinline__ void dmma(double &d0, double &d1, double a, double b)
+{
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(256) dmma2d_sweep(const double *__restrict__ in, double *__restrict__ out,
+                                                    const __grid_constant__ TcParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int R = p.R, lines = 2 * R + 1, nkb = p.nkb;  // K step 4
+    const int W = DM_T + 8 * 0 + p.nch;                  // smem row length (doubles)
+    const int H = DM_T + 2 * R;
+    double *S = reinterpret_cast<double *>(smem_raw);
+    double *Bf = S + (size_t)H * W;  // [ai][kb][lane] fragments: B[lane%4][lane/4]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t Y0 = p.rh + (int64_t)blockIdx.y * DM_T;
+    const int64_t X0 = p.rh + (int64_t)blockIdx.x * DM_T;
+    const int64_t ny = p.Ey - 2 * p.rh, nx = p.Ex - 2 * p.rh;
+
+    for (int idx = tid; idx < lines * nkb * 32; idx += blockDim.x) {
+        const int l = idx % 32, blk = idx / 32;
+        const int ai = blk / nkb, kb = blk % nkb;
+        const int k = kb * 4 + (l & 3), n = l >> 2;
+        const int b = k - n - R;
+        Bf[idx] = (b >= -R && b <= R) ? p.w[ai * lines + (b + R)] : 0.0;
+    }
+    for (int row = warp; row < H; row += 8) {
+        const int64_t gy = Y0 - R + row;
+        const bool rowok = gy >= 0 && gy < p.Ey;
+        for (int x = lane; x < W; x += 32) {
+            const int64_t gx = X0 - R + x;
+            S[row * W + x] = (rowok && gx >= 0 && gx < p.Ex) ? __ldg(in + gy * p.Ex + gx) : 0.0;
+        }
+    }
+    __syncthreads();
+
+    const int g = lane >> 2, c = lane & 3;
+    double acc[8][2];
+#pragma unroll
+    for (int nb = 0; nb < 8; ++nb) acc[nb][0] = acc[nb][1] = 0.0;
+    for (int ai = 0; ai < lines; ++ai) {
+        const double *srow = S + (warp * 8 + g + ai) * W + c;
+        for (int kb = p.kb_lo[ai]; kb <= p.kb_hi[ai]; ++kb) {
+            const double b = Bf[(ai * nkb + kb) * 32 + lane];
+#pragma unroll
+            for (int nb = 0; nb < 8; ++nb) dmma(acc[nb][0], acc[nb][1], srow[nb * 8 + kb * 4], b);
+        }
+    }
+    const int64_t gy = Y0 + warp * 8 + g, iy = gy - p.rh;
+    if (iy < ny) {
+#pragma unroll
+        for (int nb = 0; nb < 8; ++nb) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t ix = X0 - p.rh + nb * 8 + 2 * c + h;
+                if (ix < nx && outside_band(iy, ix, ny, nx, p.band)) out[gy * p.Ex + p.rh + ix] = acc[nb][h];
+            }
+        }
+    }
+}
+
+}  // namespace tcs
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+stencil_status fill_params(const Plan &p, int t, int n_tile, int k_inst, TcParams *tp, TcLines *L)
+{
+    const int r = p.pat.r, R = t * r;
+    if (R > kTcMaxR) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: fused radius t*r must be <= 12");
+    *L = tc_lines_2d(p.pat.shape, r, t, n_tile, k_inst);
+    std::vector<double> wt = compose_dense(p.pat, p.w, t);
+    std::memset(tp, 0, sizeof(*tp));
+    const int lines = 2 * R + 1;
+    for (int i = 0; i < lines * lines; i++) tp->w[i] = wt[i];
+    for (int a = 0; a < lines; a++) {
+        tp->kb_lo[a] = (unsigned char)L->kb_lo[a];
+        tp->kb_hi[a] = (unsigned char)L->kb_hi[a];
+        if (L->kb_lo[a] > L->kb_hi[a]) {  // empty line
+            tp->kb_lo[a] = 1;
+            tp->kb_hi[a] = 0;
+        }
+    }
+    tp->R = R;
+    tp->rh = r;
+    tp->band = (t - 1) * r;
+    tp->nkb = L->nkb;
+    tp->Ey = p.ext[1];
+    tp->Ex = p.ext[2];
+    return STENCIL_OK;
+}
+
+template <int PREC, int NACC>
+stencil_status launch_tc2d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+{
+    using namespace tcs;
+    constexpr int ES = Elem<PREC>::bytes, E = 16 / ES, KI = 2 * E, TX = NACC * TN;
+    static int cached = 0;
+    TcParams tp;
+    TcLines L;
+    stencil_status s = fill_params(p, t, TN, KI, &tp, &L);
+    if (s != STENCIL_OK) return s;
+    const int R = tp.R;
+    tp.hs = TM + 2 * R;
+    if (tp.hs % 2 == 0) tp.hs += 1;  // odd chunk-column height: conflict-free staging stores
+    tp.nch = (TN * (NACC - 1) + L.kext) / E;
+    const bool split = PREC != P_TF32;
+    const size_t a_bytes = (size_t)tp.nch * tp.hs * 16;
+    const size_t b_bytes = (size_t)(2 * R + 1) * L.nkb * 256;
+    size_t smem = (a_bytes + b_bytes) * (split ? 2 : 1);
+    const size_t stage = (size_t)TM * (TX + 4) * 4;
+    if (smem < stage) smem = stage;
+    smem += 128;  // TMEM address and mbarrier in front of the operands
+    if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core tile does not fit in shared memory");
+    auto kern = tc2d_sweep<PREC, NACC>;
+    s = ensure_smem((const void *)kern, smem, &cached);
+    if (s != STENCIL_OK) return s;
+    const int64_t ny = p.dims[1], nx = p.dims[2];
+    dim3 grid((unsigned)((nx + TX - 1) / TX), (unsigned)((ny + TM - 1) / TM));
+    kern<<<grid, 128, smem, st>>>((const float *)in, (float *)out, tp);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_sweep launch");
+}
+
+stencil_status launch_dmma2d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+{
+    using namespace tcs;
+    static int cached = 0;
+    TcParams tp;
+    TcLines L;
+    stencil_status s = fill_params(p, t, 8, 4, &tp, &L);
+    if (s != STENCIL_OK) return s;
+    const int R = tp.R;
+    // smem row: the widest window read is 8*7 + kext columns
+    tp.nch = 8 * 7 + L.kext - DM_T;  // extra columns beyond DM_T
+    if (tp.nch < 0) tp.nch = 0;
+    const int W = DM_T + tp.nch, H = DM_T + 2 * R;
+    const size_t smem = ((size_t)H * W + (size_t)(2 * R + 1) * L.nkb * 32) * 8;
+    if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "FP64 MMA tile does not fit in shared memory");
+    s = ensure_smem((const void *)dmma2d_sweep, smem, &cached);
+    if (s != STENCIL_OK) return s;
+    const int64_t ny = p.dims[1], nx = p.dims[2];
+    dim3 grid((unsigned)((nx + DM_T - 1) / DM_T), (unsigned)((ny + DM_T - 1) / DM_T));
+    dmma2d_sweep<<<grid, 256, smem, st>>>((const double *)in, (double *)out, tp);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "dmma2d_sweep launch");
+}
+
+}  // namespace
+
+stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+{
+    if (p.pat.d != 2) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: 2-D grids only");
+    stencil_status s;
+    if (p.dtype == STENCIL_F64) {
+        s = launch_dmma2d(p, in, out, t, st);
+    } else {
+        switch (p.precision) {
+        case STENCIL_PREC_TF32: s = launch_tc2d<tcs::P_TF32, 16>(p, in, out, t, st); break;
+        case STENCIL_PREC_TF32X3: s = launch_tc2d<tcs::P_TF32X3, 8>(p, in, out, t, st); break;
+        case STENCIL_PREC_BF16X3: s = launch_tc2d<tcs::P_BF16X3, 16>(p, in, out, t, st); break;
+        default: return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: precision");
+        }
+    }
+    if (s != STENCIL_OK || t == 1) return s;
+    // points within (t-1) r of the boundary: stepwise on CUDA cores
+    return launch_cu_band(p, in, out, t, (t - 1) * p.pat.r, st);
+}
+
+stencil_status read_device_error(int *flag)
+{
+    int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
+    if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    *flag = v;
+    return STENCIL_OK;
+}
+
+}  // namespace gbs

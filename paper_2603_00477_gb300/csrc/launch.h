@@ -11,6 +11,18 @@ namespace gbs {
 // points only; halo cells of out are left untouched).
 stencil_status launch_cu_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
 
+// One fused sweep of depth t on CUDA cores that writes only the interior
+// points closer than `band` to the boundary (after a tensor-core sweep).
+stencil_status launch_cu_band(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+
+// One fused sweep of depth t on the tensor-core path (FP32: tcgen05 with the
+// plan's precision form; FP64: FP64 MMA), followed by the band sweep if t > 1.
+stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
+
+// Read and clear the device error word the tensor-core kernels set when a
+// bounded wait runs out (1 = timed out).
+stencil_status read_device_error(int *flag);
+
 // Copy the halo cells (the fixed boundary) of `in` to `out` and, if not null,
 // to `out2`.
 stencil_status launch_halo_copy(const Plan &p, const void *in, void *out, void *out2, cudaStream_t st);

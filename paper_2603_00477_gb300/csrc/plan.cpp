@@ -17,6 +17,7 @@
 #include <string>
 
 #include "internal.h"
+#include "tc_layout.h"
 
 namespace gbs {
 
@@ -112,9 +113,19 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
 {
     TcGeometry g;
     g.n_tile = 8;
-    if (dtype == STENCIL_F64) g.k_inst = 4;                 // FP64 MMA m8n8k4
+    if (dtype == STENCIL_F64) g.k_inst = 4;                    // FP64 MMA m8n8k4
     else if (precision == STENCIL_PREC_BF16X3) g.k_inst = 16;  // kind::f16 K = 16
-    else g.k_inst = 8;                                      // kind::tf32 K = 8
+    else g.k_inst = 8;                                         // kind::tf32 K = 8
+    (void)path;
+    if (d == 2) {
+        TcLines L = tc_lines_2d(shape, r, t, g.n_tile, g.k_inst);
+        g.kext = L.kext;
+        g.sparsity = L.sparsity();
+        g.available = t * r <= 12;
+        return g;
+    }
+    // 3-D (model only): every (plane, row) line of the composite issues its
+    // padded window
     std::vector<int> half;
     composite_lines(shape, d, r, t, &half);
     double useful = 0, issued = 0;
@@ -127,17 +138,16 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     }
     g.kext = kmax;
     g.sparsity = issued > 0 ? useful / issued : 0;
-    (void)path;
     return g;
 }
 
-// Tensor-core kernels present in this build.
+// Tensor-core kernels present in this build: 2-D, fused radius t*r <= 12;
+// FP64 grids on the FP64 MMA, FP32 grids in the TF32 / TF32X3 / BF16X3 forms.
 bool tc_supported(const Plan &p, int precision, int path)
 {
-    (void)p;
-    (void)precision;
-    (void)path;
-    return false;
+    if (path != STENCIL_PATH_TENSOR_CORE || p.pat.d != 2) return false;
+    if (p.dtype == STENCIL_F64) return precision == STENCIL_PREC_NATIVE;
+    return precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3;
 }
 
 static double tc_peak(const Plan &p, int precision, int path)
@@ -197,6 +207,7 @@ stencil_status dispatch(Plan *p)
             int t_lo = p->req_t ? p->req_t : 1;
             int t_hi = p->req_t ? p->req_t : max_fused_t(*p, path);
             for (int t = t_lo; t <= t_hi; t++) {
+                if (path != STENCIL_PATH_CUDA_CORE && t * r > 12) continue;
                 Cand c{path, prec, t, 0.0, {1, 1, 1}};
                 if (path == STENCIL_PATH_CUDA_CORE) {
                     if (p->req_tile[0] || p->req_tile[1] || p->req_tile[2]) {
@@ -210,6 +221,9 @@ stencil_status dispatch(Plan *p)
                     double mem = t * B / (2.0 * D) / 1e9;
                     c.gst = std::min(comp, mem);
                 } else {
+                    c.tile[0] = 1;
+                    c.tile[1] = p->dtype == STENCIL_F64 ? 64 : 128;
+                    c.tile[2] = p->dtype == STENCIL_F64 ? 64 : (prec == STENCIL_PREC_TF32X3 ? 64 : 128);
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec), P_cu,
                                             tc_peak(*p, prec, path), B);
@@ -416,6 +430,43 @@ stencil_status stencil_plan_set_workspace(stencil_plan *plan, void *dev_ptr, siz
     if (!dev_ptr && bytes > 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_workspace: null with bytes > 0");
     plan->p.ws = dev_ptr;
     plan->p.ws_bytes = dev_ptr ? bytes : 0;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_tc_layout *layout, int *kb_lo,
+                                      int *kb_hi, double *B)
+{
+    if (!plan || !layout) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_tc_layout: null argument");
+    const Plan &p = plan->p;
+    if (t < 1 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_tc_layout: t must be 1..16");
+    int prec = p.dtype == STENCIL_F64 ? STENCIL_PREC_NATIVE : p.precision;
+    if (p.dtype == STENCIL_F32 && prec == STENCIL_PREC_NATIVE) prec = STENCIL_PREC_TF32;
+    if (!tc_supported(p, prec, STENCIL_PATH_TENSOR_CORE) || t * p.pat.r > 12)
+        return fail(STENCIL_ERR_UNSUPPORTED, "stencil_plan_tc_layout: no tensor-core kernel for this plan and t");
+    TcGeometry g = tc_geometry(p.pat.shape, p.pat.d, p.pat.r, t, p.dtype, prec, STENCIL_PATH_TENSOR_CORE);
+    TcLines L = tc_lines_2d(p.pat.shape, p.pat.r, t, g.n_tile, g.k_inst);
+    layout->R = L.R;
+    layout->n_tile = L.n_tile;
+    layout->k_inst = L.k_inst;
+    layout->kext = L.kext;
+    layout->nkb = L.nkb;
+    layout->sparsity = L.sparsity();
+    const int lines = 2 * L.R + 1;
+    for (int a = 0; a < lines; a++) {
+        if (kb_lo) kb_lo[a] = L.kb_lo[a];
+        if (kb_hi) kb_hi[a] = L.kb_hi[a];
+    }
+    if (B) {
+        std::vector<double> wt = compose_dense(p.pat, p.w, t);
+        size_t i = 0;
+        for (int a = 0; a < lines; a++)
+            for (int kb = 0; kb < L.nkb; kb++)
+                for (int k = 0; k < L.k_inst; k++)
+                    for (int n = 0; n < L.n_tile; n++) {
+                        const int b = kb * L.k_inst + k - n - L.R;
+                        B[i++] = (b >= -L.R && b <= L.R) ? wt[(size_t)a * lines + (b + L.R)] : 0.0;
+                    }
+    }
     return STENCIL_OK;
 }
 

@@ -1,0 +1,69 @@
+// probe.cu -- measured FMA-pipe peaks (the P_CU of the paper's Table 1 for
+// this GPU): independent FMA chains in registers, timed with CUDA events.
+#include <cuda_runtime.h>
+
+#include "launch.h"
+
+namespace gbs {
+namespace {
+
+__device__ unsigned long long g_probe_sink;
+
+template <typename T>
+__global__ void __launch_bounds__(256) fma_chains(int iters, T seed)
+{
+    T a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed + (T)(threadIdx.x + j);
+    const T m = (T)0.999999, c = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == (T)-12345.0) g_probe_sink = 1;  // never true; keeps the chains alive
+}
+
+template <typename T>
+stencil_status time_chains(int blocks, int iters, cudaStream_t st, double *flops_per_s)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(STENCIL_ERR_CUDA, "cudaEventCreate");
+    fma_chains<T><<<blocks, 256, 0, st>>>(iters / 8, (T)0.5);  // warm-up
+    note_launch();
+    cudaEventRecord(e0, st);
+    fma_chains<T><<<blocks, 256, 0, st>>>(iters, (T)0.5);
+    note_launch();
+    cudaEventRecord(e1, st);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "probe timing");
+    *flops_per_s = (double)blocks * 256.0 * iters * 8.0 * 2.0 / (ms * 1e-3);
+    return STENCIL_OK;
+}
+
+}  // namespace
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_stream_t stream)
+{
+    if (!measured) return fail(STENCIL_ERR_INVALID_ARG, "stencil_probe_peaks: null pointer");
+    *measured = stencil_peaks{};
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_probe_peaks: device query");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = sms * 4;
+    stencil_status s = time_chains<double>(blocks, 1 << 8, st, &measured->cu_f64_flops);
+    if (s != STENCIL_OK) return s;
+    return time_chains<float>(blocks, 1 << 14, st, &measured->cu_f32_flops);
+}

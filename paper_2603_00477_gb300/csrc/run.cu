@@ -93,8 +93,10 @@ static stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, s
         const int tk = (k == nsweeps - 1 && rem) ? rem : t;
         if (p.path == STENCIL_PATH_CUDA_CORE) {
             s = launch_cu_sweep(p, src, dst, tk, st);
+        } else if (p.path == STENCIL_PATH_TENSOR_CORE) {
+            s = launch_tc_sweep(p, src, dst, tk, st);
         } else {
-            s = fail(STENCIL_ERR_UNSUPPORTED, "path not built");
+            s = fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path not built");
         }
         if (s != STENCIL_OK) return s;
         src = dst;
@@ -140,4 +142,15 @@ extern "C" stencil_status stencil_run_host(stencil_plan *plan, const void *host_
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(device -> host)");
     e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+extern "C" stencil_status stencil_device_status(stencil_stream_t stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_device_status: stream");
+    int flag = 0;
+    stencil_status s = read_device_error(&flag);
+    if (s != STENCIL_OK) return s;
+    if (flag) return fail(STENCIL_ERR_TIMEOUT, "a tensor-core kernel's bounded wait for its MMAs ran out");
+    return STENCIL_OK;
 }
