@@ -217,6 +217,58 @@ stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_t
 /* Release a plan (never frees caller workspace).  Null is ignored. */
 void stencil_plan_destroy(stencil_plan *plan);
 
+/* ---- batched form ------------------------------------------------------ */
+
+/* One 2-D grid of a batch: shape, radius (1..3), interior extents and its K
+ * weights (copied at creation). */
+typedef struct {
+    int shape;              /* STENCIL_BOX or STENCIL_STAR */
+    int r;                  /* 1..3                        */
+    int64_t ny, nx;         /* interior extents, >= 1      */
+    const double *weights;  /* K weights, offset order     */
+} stencil_grid_desc;
+
+typedef struct stencil_batch stencil_batch;
+
+/* Many independent 2-D grids of uneven size and mixed stencils, all of one
+ * dtype, run together: one persistent launch whose CTAs pull (grid, tile,
+ * sweep) work items from a device queue; an item of sweep s waits (bounded)
+ * for every tile of sweep s-1 of its grid.  Each grid gets the CUDA-core
+ * fusion depth and tile the model picks for it (t = 0) or the given t.
+ * Host only.  INVALID_ARG for bad arguments, UNSUPPORTED for r > 3. */
+stencil_status stencil_batch_create(stencil_batch **batch, int n, const stencil_grid_desc *grids,
+                                    stencil_dtype dtype, int t);
+
+/* Device workspace a run of `steps` steps needs: tables, work list, counters
+ * and one ping-pong grid per grid that takes more than one sweep. */
+size_t stencil_batch_workspace_bytes(const stencil_batch *batch, int64_t steps);
+
+/* Caller-owned device workspace (never freed here). */
+stencil_status stencil_batch_set_workspace(stencil_batch *batch, void *dev_ptr, size_t bytes);
+
+/* The plan information (t, tile, model) of grid i. */
+stencil_status stencil_batch_info(const stencil_batch *batch, int i, stencil_info *info);
+
+/* Run `steps` steps on every grid: ins[i] / outs[i] are device buffers of
+ * grid i's stored size (host arrays of n pointers).  Uploads the run's tables
+ * into the workspace (synchronising `stream` once), then launches the
+ * persistent kernel.  OOM if the workspace is too small. */
+stencil_status stencil_batch_run(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
+                                 stencil_stream_t stream);
+
+/* Same, through a CUDA graph: the first call for a given (ins, outs, steps,
+ * workspace, stream) uploads the tables and captures the counter reset and
+ * the persistent kernel into a graph; later identical calls only replay it.
+ * `stream` must not be the legacy default stream. */
+stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *ins, void *const *outs,
+                                       int64_t steps, stencil_stream_t stream);
+
+/* Synchronise `stream` and report STENCIL_ERR_TIMEOUT if the last run gave
+ * up a dependency wait (its outputs are then incomplete). */
+stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t stream);
+
+void stencil_batch_destroy(stencil_batch *batch);
+
 /* ---- model ------------------------------------------------------------- */
 
 /* The paper's model for one configuration (Sec. 3.2 Eqs. 6-12, Sec. 4.1

@@ -52,6 +52,11 @@ class stencil_tc_layout(ctypes.Structure):
                 ("nkb", ctypes.c_int), ("sparsity", ctypes.c_double)]
 
 
+class stencil_grid_desc(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int), ("r", ctypes.c_int), ("ny", ctypes.c_int64), ("nx", ctypes.c_int64),
+                ("weights", ctypes.POINTER(ctypes.c_double))]
+
+
 class stencil_model_in(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("d", ctypes.c_int), ("r", ctypes.c_int), ("t", ctypes.c_int),
                 ("dtype_bytes", ctypes.c_int), ("sparsity", ctypes.c_double), ("beta", ctypes.c_double),
@@ -113,6 +118,23 @@ def load() -> ctypes.CDLL:
     L.stencil_plan_tc_layout.restype = st
     L.stencil_device_status.argtypes = [vp]
     L.stencil_device_status.restype = st
+    L.stencil_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(stencil_grid_desc),
+                                       ctypes.c_int, ctypes.c_int]
+    L.stencil_batch_create.restype = st
+    L.stencil_batch_workspace_bytes.argtypes = [vp, i64]
+    L.stencil_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.stencil_batch_set_workspace.argtypes = [vp, vp, ctypes.c_size_t]
+    L.stencil_batch_set_workspace.restype = st
+    L.stencil_batch_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(stencil_info)]
+    L.stencil_batch_info.restype = st
+    L.stencil_batch_run.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, vp]
+    L.stencil_batch_run.restype = st
+    L.stencil_batch_run_graph.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i64, vp]
+    L.stencil_batch_run_graph.restype = st
+    L.stencil_batch_status.argtypes = [vp, vp]
+    L.stencil_batch_status.restype = st
+    L.stencil_batch_destroy.argtypes = [vp]
+    L.stencil_batch_destroy.restype = None
     L.stencil_status_string.argtypes = [ctypes.c_int]
     L.stencil_status_string.restype = ctypes.c_char_p
     L.stencil_last_error.argtypes = []
@@ -328,6 +350,105 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             stencil_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched form ---------------------------------------------------------------
+
+def stencil_batch_create(grids, dtype, t: int = 0) -> int:
+    """grids: iterable of (shape, r, ny, nx, weights)."""
+    grids = list(grids)
+    keep = []
+    arr = (stencil_grid_desc * len(grids))()
+    for i, (shape, r, ny, nx, w) in enumerate(grids):
+        wa = (ctypes.c_double * len(w))(*[float(x) for x in w])
+        keep.append(wa)
+        arr[i] = stencil_grid_desc(_shape_code(shape), int(r), int(ny), int(nx),
+                                   ctypes.cast(wa, ctypes.POINTER(ctypes.c_double)))
+    h = ctypes.c_void_p()
+    _check(load().stencil_batch_create(ctypes.byref(h), len(grids), arr, _dtype_code(dtype), int(t)),
+           "stencil_batch_create")
+    return h.value
+
+
+def stencil_batch_workspace_bytes(batch: int, steps: int) -> int:
+    return int(load().stencil_batch_workspace_bytes(batch, int(steps)))
+
+
+def stencil_batch_set_workspace(batch: int, dev_ptr: int, nbytes: int) -> None:
+    _check(load().stencil_batch_set_workspace(batch, dev_ptr, nbytes), "stencil_batch_set_workspace")
+
+
+def stencil_batch_info(batch: int, i: int) -> dict:
+    info = stencil_info()
+    _check(load().stencil_batch_info(batch, int(i), ctypes.byref(info)), "stencil_batch_info")
+    out = {f: getattr(info, f) for f, _ in stencil_info._fields_}
+    out["tile"] = list(info.tile)
+    return out
+
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[int(p) for p in ptrs])
+
+
+def stencil_batch_run(batch: int, in_ptrs, out_ptrs, steps: int, stream=None) -> None:
+    _check(load().stencil_batch_run(batch, _ptr_array(in_ptrs), _ptr_array(out_ptrs), int(steps),
+                                    _stream_handle(stream)), "stencil_batch_run")
+
+
+def stencil_batch_run_graph(batch: int, in_ptrs, out_ptrs, steps: int, stream=None) -> None:
+    _check(load().stencil_batch_run_graph(batch, _ptr_array(in_ptrs), _ptr_array(out_ptrs), int(steps),
+                                          _stream_handle(stream)), "stencil_batch_run_graph")
+
+
+def stencil_batch_status(batch: int, stream=None) -> None:
+    _check(load().stencil_batch_status(batch, _stream_handle(stream)), "stencil_batch_status")
+
+
+def stencil_batch_destroy(batch: int) -> None:
+    if batch:
+        load().stencil_batch_destroy(batch)
+
+
+class Batch:
+    """A batch of 2-D grids with PyTorch-allocated workspace."""
+
+    def __init__(self, grids, dtype, t: int = 0):
+        self.grids = [(g[0], int(g[1]), int(g[2]), int(g[3]), g[4]) for g in grids]
+        self.dtype = "f64" if _dtype_code(dtype) == F64 else "f32"
+        self.handle = stencil_batch_create(self.grids, dtype, t)
+        self._ws = None
+        self._ws_steps = None
+
+    def stored_shape(self, i):
+        _, r, ny, nx, _ = self.grids[i]
+        return (ny + 2 * r, nx + 2 * r)
+
+    def info(self, i):
+        return stencil_batch_info(self.handle, i)
+
+    def ensure_workspace(self, steps, device="cuda"):
+        import torch
+        need = stencil_batch_workspace_bytes(self.handle, steps)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+            stencil_batch_set_workspace(self.handle, self._ws.data_ptr(), self._ws.numel())
+        return self._ws
+
+    def run(self, ins, outs, steps: int, stream=None, graph: bool = False):
+        self.ensure_workspace(steps, ins[0].device)
+        fn = stencil_batch_run_graph if graph else stencil_batch_run
+        fn(self.handle, [x.data_ptr() for x in ins], [y.data_ptr() for y in outs], steps, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stencil_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

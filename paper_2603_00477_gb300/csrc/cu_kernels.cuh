@@ -73,208 +73,311 @@ struct Weights {
 // tensor-core sweep, whose fused kernel is exact only away from the
 // boundary.
 struct Ring {
-    int band;        // 0: whole grid (2-D launch grid)
+    int band;        // 0: every tile, row-major over ntx columns
     int nty, ntx;    // tiles along y and x
-    int rows_tb;     // tile rows taken whole (top + bottom)
-    int by_w;        // top ring rows
-    int cols_lr;     // tile columns taken in the middle rows (left + right)
-    int bx_w;        // left ring columns
+    int rows_tb;     // tile rows taken whole: min(nty, top_w + bottom rows)
+    int top_w;       // tile rows touching the top band
+    int cols_lr;     // tile columns taken in the other rows: min(ntx, left_w + right cols)
+    int left_w;      // tile columns touching the left band
 };
 
+// Tile id -> (tile row, tile column): first the whole tile rows (the top_w
+// top ones, then the bottom ones), then, row by row, the left and right tile
+// columns of the remaining rows.
 __device__ __forceinline__ void ring_tile(const Ring &g, int id, int *by, int *bx)
 {
     if (id < g.rows_tb * g.ntx) {
         const int rr = id / g.ntx;
         *bx = id % g.ntx;
-        *by = rr < g.by_w ? rr : g.nty - g.rows_tb + rr;
+        *by = rr < g.top_w ? rr : g.nty - g.rows_tb + rr;
     } else {
         const int id2 = id - g.rows_tb * g.ntx;
         const int cc = id2 % g.cols_lr;
-        *by = g.by_w + id2 / g.cols_lr;
-        *bx = cc < g.bx_w ? cc : g.ntx - g.cols_lr + cc;
+        *by = g.top_w + id2 / g.cols_lr;
+        *bx = cc < g.left_w ? cc : g.ntx - g.cols_lr + cc;
     }
 }
 
-template <typename T, int SHAPE, int R, int V>
-__global__ void __launch_bounds__(kThreads)
-    cu2d_sweep(const T *__restrict__ in, T *__restrict__ out, const Weights<T, Taps<SHAPE, 2, R>::K> wt,
-               int64_t Ey, int64_t Ex, int BY, int BX, int t, const Ring ring)
+// Asynchronous global -> shared copy of one element (cp.async, L1-allocating);
+// src_bytes = 0 writes zeros without reading global memory.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void *smem_dst, const void *gmem_src, bool valid)
 {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    const int n = valid ? BYTES : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(gmem_src), "n"(BYTES), "r"(n)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Persistent form: CTA b processes tiles b, b + gridDim.x, ...; while it
+// computes one tile it prefetches the next into the other staging buffer
+// with cp.async, so the FMA pipe never waits for a synchronous load phase.
+// Shared memory: two staging buffers (H x W) and, for t > 1, a work buffer
+// for the intermediate sub-steps.
+// FP64 kernels read their weights from shared memory (one LDS per FMA is
+// free next to the FP64 pipe, and keeping K doubles in registers across the
+// persistent loop would spill); FP32 kernels read them from the constant bank.
+template <typename T, int K>
+__host__ __device__ constexpr int weight_smem_bytes()
+{
+    return sizeof(T) == 8 ? (int)((K * sizeof(T) + 15) / 16 * 16) : 0;
+}
+
+template <typename T, int SHAPE, int R, int V>
+__global__ void __launch_bounds__(kThreads, 2)
+    cu2d_sweep(const T *__restrict__ in, T *__restrict__ out,
+               const __grid_constant__ Weights<T, Taps<SHAPE, 2, R>::K> wt, int64_t Ey, int64_t Ex, int BY, int BX,
+               int t, const Ring ring, int ntiles)
+{
+    constexpr int KT = Taps<SHAPE, 2, R>::K;
+    constexpr bool kSmemW = sizeof(T) == 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *wsm = reinterpret_cast<T *>(smem_raw);
+    if (kSmemW) {
+        for (int k = threadIdx.x; k < KT; k += blockDim.x) wsm[k] = wt.w[k];
+    }
+    unsigned char *base = smem_raw + weight_smem_bytes<T, KT>();
     const int H = BY + 2 * t * R, W = BX + 2 * t * R;
-    T *bufA = reinterpret_cast<T *>(smem_raw);
-    T *bufB = bufA + (size_t)H * W;
-    int tby = blockIdx.y, tbx = blockIdx.x;
-    if (ring.band > 0) ring_tile(ring, blockIdx.x, &tby, &tbx);
-    const int64_t Y0 = R + (int64_t)tby * BY - (int64_t)t * R;
-    const int64_t X0 = R + (int64_t)tbx * BX - (int64_t)t * R;
+    const size_t buf = (size_t)H * W;
+    T *stage[2] = {reinterpret_cast<T *>(base), reinterpret_cast<T *>(base) + buf};
+    T *work = reinterpret_cast<T *>(base) + 2 * buf;
     const int64_t ny = Ey - 2 * R, nx = Ex - 2 * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-    // Stage the dependency region; cells outside the stored array read 0
-    // and are never used by an interior point.
-    for (int y = warp; y < H; y += nwarps) {
-        const int64_t gy = Y0 + y;
-        const bool rowok = gy >= 0 && gy < Ey;
-        const T *src = in + gy * Ex;
-        for (int x = lane; x < W; x += 32) {
-            const int64_t gx = X0 + x;
-            bufA[y * W + x] = (rowok && gx >= 0 && gx < Ex) ? __ldg(src + gx) : T(0);
+    auto origin = [&](int id, int64_t *Y0, int64_t *X0) {
+        int by, bx;
+        if (ring.band > 0) {
+            ring_tile(ring, id, &by, &bx);
+        } else {
+            by = id / ring.ntx;
+            bx = id % ring.ntx;
         }
-    }
-    __syncthreads();
+        *Y0 = R + (int64_t)by * BY - (int64_t)t * R;
+        *X0 = R + (int64_t)bx * BX - (int64_t)t * R;
+    };
+    // Stage the dependency region of a tile; cells outside the stored array
+    // are zero-filled and never used by an interior point.
+    auto prefetch = [&](int id, T *dst) {
+        int64_t Y0, X0;
+        origin(id, &Y0, &X0);
+        for (int y = warp; y < H; y += nwarps) {
+            const int64_t gy = Y0 + y;
+            const bool rowok = gy >= 0 && gy < Ey;
+            for (int x = lane; x < W; x += 32) {
+                const int64_t gx = X0 + x;
+                const bool ok = rowok && gx >= 0 && gx < Ex;
+                cp_async_elem<sizeof(T)>(dst + y * W + x, ok ? in + gy * Ex + gx : in, ok);
+            }
+        }
+    };
 
-    T *src = bufA, *dst = bufB;
-    for (int s = 1; s <= t; ++s) {
-        const int lo = s * R;
-        const int hiY = H - s * R, hiX = W - s * R;
-        const int cw = hiX - lo, ch = hiY - lo;
-        const int strips = (ch + V - 1) / V;
-        const bool last = s == t;
-        for (int item = threadIdx.x; item < cw * strips; item += blockDim.x) {
-            const int x = lo + item % cw;
-            const int y0 = lo + (item / cw) * V;
-            T acc[V];
+    int cur = 0;
+    if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, stage[0]);
+    cp_async_commit();
+    for (int id = blockIdx.x; id < ntiles; id += gridDim.x) {
+        const int nid = id + gridDim.x;
+        if (nid < ntiles) prefetch(nid, stage[cur ^ 1]);
+        cp_async_commit();
+        cp_async_wait_group<1>();  // this tile's copies (all but the newest group) have landed
+        __syncthreads();
+        int64_t Y0, X0;
+        origin(id, &Y0, &X0);
+
+        T *src = stage[cur], *dst = work;
+        for (int s = 1; s <= t; ++s) {
+            const int lo = s * R;
+            const int hiY = H - s * R, hiX = W - s * R;
+            const int cw = hiX - lo, ch = hiY - lo;
+            const int strips = (ch + V - 1) / V;
+            const bool last = s == t;
+            for (int item = threadIdx.x; item < cw * strips; item += blockDim.x) {
+                const int x = lo + item % cw;
+                const int y0 = lo + (item / cw) * V;
+                T acc[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) acc[j] = T(0);
+                for (int j = 0; j < V; ++j) acc[j] = T(0);
 #pragma unroll
-            for (int q = 0; q < V + 2 * R; ++q) {
-                const int yy = y0 - R + q;
-                if (yy < H) {
-                    const T *row = src + yy * W + x;
-                    T v[2 * R + 1];
+                for (int q = 0; q < V + 2 * R; ++q) {
+                    const int yy = y0 - R + q;
+                    if (yy < H) {
+                        const T *row = src + yy * W + x;
+                        T v[2 * R + 1];
 #pragma unroll
-                    for (int c = 0; c < 2 * R + 1; ++c) v[c] = row[c - R];
+                        for (int c = 0; c < 2 * R + 1; ++c) v[c] = row[c - R];
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const int oy = q - R - j;
-                        if (oy >= -R && oy <= R) {
+                        for (int j = 0; j < V; ++j) {
+                            const int oy = q - R - j;
+                            if (oy >= -R && oy <= R) {
 #pragma unroll
-                            for (int ox = -R; ox <= R; ++ox) {
-                                const int k = tap_index<SHAPE, 2, R>(0, oy, ox);
-                                if (k >= 0) acc[j] = fma(wt.w[k], v[ox + R], acc[j]);
+                                for (int ox = -R; ox <= R; ++ox) {
+                                    const int k = tap_index<SHAPE, 2, R>(0, oy, ox);
+                                    if (k >= 0) acc[j] = fma(kSmemW ? wsm[k] : wt.w[k], v[ox + R], acc[j]);
+                                }
                             }
                         }
                     }
                 }
-            }
-            const int64_t gx = X0 + x;
-            const bool colint = gx >= R && gx < Ex - R;
+                const int64_t gx = X0 + x;
+                const bool colint = gx >= R && gx < Ex - R;
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const int y = y0 + j;
-                if (y < hiY) {
-                    const int64_t gy = Y0 + y;
-                    const bool interior = colint && gy >= R && gy < Ey - R;
-                    if (last) {
-                        bool keep = interior;
-                        if (ring.band > 0) {
-                            const int64_t iy = gy - R, ix = gx - R;
-                            keep = keep && (iy < ring.band || ix < ring.band || ny - 1 - iy < ring.band ||
-                                            nx - 1 - ix < ring.band);
+                for (int j = 0; j < V; ++j) {
+                    const int y = y0 + j;
+                    if (y < hiY) {
+                        const int64_t gy = Y0 + y;
+                        const bool interior = colint && gy >= R && gy < Ey - R;
+                        if (last) {
+                            bool keep = interior;
+                            if (ring.band > 0) {
+                                const int64_t iy = gy - R, ix = gx - R;
+                                keep = keep && (iy < ring.band || ix < ring.band || ny - 1 - iy < ring.band ||
+                                                nx - 1 - ix < ring.band);
+                            }
+                            if (keep) out[gy * Ex + gx] = acc[j];
+                        } else {
+                            dst[y * W + x] = interior ? acc[j] : src[y * W + x];
                         }
-                        if (keep) out[gy * Ex + gx] = acc[j];
-                    } else {
-                        dst[y * W + x] = interior ? acc[j] : src[y * W + x];
                     }
                 }
             }
+            __syncthreads();
+            // next sub-step reads what this one wrote; the staged input is no
+            // longer needed after the first sub-step, so it becomes the target
+            T *tmp = src;
+            src = dst;
+            dst = tmp;
         }
-        __syncthreads();
-        T *tmp = src;
-        src = dst;
-        dst = tmp;
+        cur ^= 1;
     }
+    cp_async_wait_group<0>();
 }
 
 // ---------------------------------------------------------------------------
 // 3-D: tile BZ x BY x BX, strips of V planes.
 // ---------------------------------------------------------------------------
 template <typename T, int SHAPE, int R, int V>
-__global__ void __launch_bounds__(kThreads)
-    cu3d_sweep(const T *__restrict__ in, T *__restrict__ out, const Weights<T, Taps<SHAPE, 3, R>::K> wt,
-               int64_t Ez, int64_t Ey, int64_t Ex, int BZ, int BY, int BX, int t, int tiles_x)
+__global__ void __launch_bounds__(kThreads, 2)
+    cu3d_sweep(const T *__restrict__ in, T *__restrict__ out,
+               const __grid_constant__ Weights<T, Taps<SHAPE, 3, R>::K> wt, int64_t Ez, int64_t Ey, int64_t Ex,
+               int BZ, int BY, int BX, int t, int tiles_x, int tiles_y, int ntiles)
 {
+    constexpr int KT = Taps<SHAPE, 3, R>::K;
+    constexpr bool kSmemW = sizeof(T) == 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *wsm = reinterpret_cast<T *>(smem_raw);
+    if (kSmemW) {
+        for (int k = threadIdx.x; k < KT; k += blockDim.x) wsm[k] = wt.w[k];
+    }
+    unsigned char *base = smem_raw + weight_smem_bytes<T, KT>();
     const int Z = BZ + 2 * t * R, H = BY + 2 * t * R, W = BX + 2 * t * R;
     const int plane = H * W;
-    T *bufA = reinterpret_cast<T *>(smem_raw);
-    T *bufB = bufA + (size_t)Z * plane;
-    const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
-    const int64_t Z0 = R + (int64_t)blockIdx.y * BZ - (int64_t)t * R;
-    const int64_t Y0 = R + (int64_t)by * BY - (int64_t)t * R;
-    const int64_t X0 = R + (int64_t)bx * BX - (int64_t)t * R;
+    const size_t buf = (size_t)Z * plane;
+    T *stage[2] = {reinterpret_cast<T *>(base), reinterpret_cast<T *>(base) + buf};
+    T *work = reinterpret_cast<T *>(base) + 2 * buf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-    for (int zy = warp; zy < Z * H; zy += nwarps) {
-        const int z = zy / H, y = zy % H;
-        const int64_t gz = Z0 + z, gy = Y0 + y;
-        const bool ok = gz >= 0 && gz < Ez && gy >= 0 && gy < Ey;
-        const T *src = in + (gz * Ey + gy) * Ex;
-        for (int x = lane; x < W; x += 32) {
-            const int64_t gx = X0 + x;
-            bufA[z * plane + y * W + x] = (ok && gx >= 0 && gx < Ex) ? __ldg(src + gx) : T(0);
+    auto origin = [&](int id, int64_t *Z0, int64_t *Y0, int64_t *X0) {
+        const int bx = id % tiles_x, by = (id / tiles_x) % tiles_y, bz = id / (tiles_x * tiles_y);
+        *Z0 = R + (int64_t)bz * BZ - (int64_t)t * R;
+        *Y0 = R + (int64_t)by * BY - (int64_t)t * R;
+        *X0 = R + (int64_t)bx * BX - (int64_t)t * R;
+    };
+    auto prefetch = [&](int id, T *dst) {
+        int64_t Z0, Y0, X0;
+        origin(id, &Z0, &Y0, &X0);
+        for (int zy = warp; zy < Z * H; zy += nwarps) {
+            const int z = zy / H, y = zy % H;
+            const int64_t gz = Z0 + z, gy = Y0 + y;
+            const bool ok = gz >= 0 && gz < Ez && gy >= 0 && gy < Ey;
+            const T *row = in + (gz * Ey + gy) * Ex;
+            for (int x = lane; x < W; x += 32) {
+                const int64_t gx = X0 + x;
+                const bool v = ok && gx >= 0 && gx < Ex;
+                cp_async_elem<sizeof(T)>(dst + z * plane + y * W + x, v ? row + gx : in, v);
+            }
         }
-    }
-    __syncthreads();
+    };
 
-    T *src = bufA, *dst = bufB;
-    for (int s = 1; s <= t; ++s) {
-        const int lo = s * R;
-        const int hiZ = Z - s * R, hiY = H - s * R, hiX = W - s * R;
-        const int cw = hiX - lo, ch = hiY - lo, cz = hiZ - lo;
-        const int strips = (cz + V - 1) / V;
-        const bool last = s == t;
-        for (int item = threadIdx.x; item < cw * ch * strips; item += blockDim.x) {
-            const int x = lo + item % cw;
-            const int y = lo + (item / cw) % ch;
-            const int z0 = lo + (item / (cw * ch)) * V;
-            T acc[V];
+    int cur = 0;
+    if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, stage[0]);
+    cp_async_commit();
+    for (int id = blockIdx.x; id < ntiles; id += gridDim.x) {
+        const int nid = id + gridDim.x;
+        if (nid < ntiles) prefetch(nid, stage[cur ^ 1]);
+        cp_async_commit();
+        cp_async_wait_group<1>();
+        __syncthreads();
+        int64_t Z0, Y0, X0;
+        origin(id, &Z0, &Y0, &X0);
+
+        T *src = stage[cur], *dst = work;
+        for (int s = 1; s <= t; ++s) {
+            const int lo = s * R;
+            const int hiZ = Z - s * R, hiY = H - s * R, hiX = W - s * R;
+            const int cw = hiX - lo, ch = hiY - lo, cz = hiZ - lo;
+            const int strips = (cz + V - 1) / V;
+            const bool last = s == t;
+            for (int item = threadIdx.x; item < cw * ch * strips; item += blockDim.x) {
+                const int x = lo + item % cw;
+                const int y = lo + (item / cw) % ch;
+                const int z0 = lo + (item / (cw * ch)) * V;
+                T acc[V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) acc[j] = T(0);
+                for (int j = 0; j < V; ++j) acc[j] = T(0);
 #pragma unroll
-            for (int q = 0; q < V + 2 * R; ++q) {
-                const int zz = z0 - R + q;
-                if (zz < Z) {
-                    const T *pl = src + zz * plane + y * W + x;
+                for (int q = 0; q < V + 2 * R; ++q) {
+                    const int zz = z0 - R + q;
+                    if (zz < Z) {
+                        const T *pl = src + zz * plane + y * W + x;
 #pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const int oz = q - R - j;
-                        if (oz >= -R && oz <= R) {
+                        for (int j = 0; j < V; ++j) {
+                            const int oz = q - R - j;
+                            if (oz >= -R && oz <= R) {
 #pragma unroll
-                            for (int oy = -R; oy <= R; ++oy) {
+                                for (int oy = -R; oy <= R; ++oy) {
 #pragma unroll
-                                for (int ox = -R; ox <= R; ++ox) {
-                                    const int k = tap_index<SHAPE, 3, R>(oz, oy, ox);
-                                    if (k >= 0) acc[j] = fma(wt.w[k], pl[oy * W + ox], acc[j]);
+                                    for (int ox = -R; ox <= R; ++ox) {
+                                        const int k = tap_index<SHAPE, 3, R>(oz, oy, ox);
+                                        if (k >= 0)
+                                            acc[j] = fma(kSmemW ? wsm[k] : wt.w[k], pl[oy * W + ox], acc[j]);
+                                    }
                                 }
                             }
                         }
                     }
                 }
-            }
-            const int64_t gx = X0 + x, gy = Y0 + y;
-            const bool lineint = gx >= R && gx < Ex - R && gy >= R && gy < Ey - R;
+                const int64_t gx = X0 + x, gy = Y0 + y;
+                const bool lineint = gx >= R && gx < Ex - R && gy >= R && gy < Ey - R;
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const int z = z0 + j;
-                if (z < hiZ) {
-                    const int64_t gz = Z0 + z;
-                    const bool interior = lineint && gz >= R && gz < Ez - R;
-                    if (last) {
-                        if (interior) out[(gz * Ey + gy) * Ex + gx] = acc[j];
-                    } else {
-                        const int o = z * plane + y * W + x;
-                        dst[o] = interior ? acc[j] : src[o];
+                for (int j = 0; j < V; ++j) {
+                    const int z = z0 + j;
+                    if (z < hiZ) {
+                        const int64_t gz = Z0 + z;
+                        const bool interior = lineint && gz >= R && gz < Ez - R;
+                        if (last) {
+                            if (interior) out[(gz * Ey + gy) * Ex + gx] = acc[j];
+                        } else {
+                            const int o = z * plane + y * W + x;
+                            dst[o] = interior ? acc[j] : src[o];
+                        }
                     }
                 }
             }
+            __syncthreads();
+            T *tmp = src;
+            src = dst;
+            dst = tmp;
         }
-        __syncthreads();
-        T *tmp = src;
-        src = dst;
-        dst = tmp;
+        cur ^= 1;
     }
+    cp_async_wait_group<0>();
 }
 
 }  // namespace cu

@@ -1,0 +1,580 @@
+// k_batch.cu -- many 2-D grids of uneven size and mixed stencils in one
+// persistent launch (the batched form), optionally replayed from a CUDA graph.
+//
+// Work list: one item per (grid, tile, sweep), ordered sweep-major (all
+// sweep-0 items of every grid, then all sweep-1 items, ...).  CTAs pull items
+// from a global atomic counter.  An item of sweep s > 0 of grid g waits until
+// every tile of sweep s-1 of g has been counted done (bounded spin); because
+// every item it waits for has a smaller index and was therefore already
+// taken by a running CTA, the wait always ends without any co-residency
+// assumption.  Each item stages its tile grown by t*r (L2-coherent loads:
+// other CTAs of the same launch produced the data), runs the grid's t
+// sub-steps on CUDA cores in shared memory (the same temporal blocking as
+// cu2d_sweep) and writes the tile.  Sweep-0 items also copy the halo cells
+// nearest to their tile from `in` to the grid's output and ping-pong buffers.
+// On a wait that runs out, the CTA sets the abort word and every CTA leaves.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cu_kernels.cuh"
+#include "launch.h"
+
+namespace gbs {
+namespace bt {
+
+constexpr int kThreads = 256;
+constexpr int kMaxR = 3;
+constexpr int kMaxK = (2 * kMaxR + 1) * (2 * kMaxR + 1);
+
+struct GridDev {
+    const void *in;
+    void *out;
+    void *pp;          // ping-pong buffer (null if the run is one sweep)
+    int64_t ey, ex;    // stored extents
+    int kind;          // shape * 4 + r
+    int t, nsweeps, rem;  // fusion depth, sweeps, last sweep depth (0 = t)
+    int ntiles, ntx, by, bx;
+    int woff;          // offset of the weights in the weight table
+    int doff;          // offset of this grid's per-sweep done counters
+};
+
+struct Item {
+    int g, tile, s, pad;
+};
+
+struct Ctl {
+    int head;   // next work item
+    int abort;  // set when a dependency wait ran out
+};
+
+constexpr unsigned long long kWaitCycles = 2ull << 30;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_l2(const T *p)
+{
+    return __ldcg(p);
+}
+
+// One item: tile `tile` of grid G, sweep s (depth t_s) from src to dst.
+template <typename T, int SHAPE, int R, int V>
+__device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *src_g, T *dst_g, int tile, int s,
+                         int ts, unsigned char *smem)
+{
+    constexpr int KT = cu::Taps<SHAPE, 2, R>::K;
+    T w[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) w[k] = wg[k];
+    const int BY = G.by, BX = G.bx;
+    const int H = BY + 2 * ts * R, W = BX + 2 * ts * R;
+    T *bufA = reinterpret_cast<T *>(smem);
+    T *bufB = bufA + (size_t)H * W;
+    const int tby = tile / G.ntx, tbx = tile % G.ntx;
+    const int64_t Ey = G.ey, Ex = G.ex, ny = Ey - 2 * R, nx = Ex - 2 * R;
+    const int64_t Y0 = R + (int64_t)tby * BY - (int64_t)ts * R;
+    const int64_t X0 = R + (int64_t)tbx * BX - (int64_t)ts * R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+
+    for (int y = warp; y < H; y += nwarps) {
+        const int64_t gy = Y0 + y;
+        const bool rowok = gy >= 0 && gy < Ey;
+        for (int x = lane; x < W; x += 32) {
+            const int64_t gx = X0 + x;
+            bufA[y * W + x] = (rowok && gx >= 0 && gx < Ex) ? ld_l2(src_g + gy * Ex + gx) : T(0);
+        }
+    }
+    __syncthreads();
+    if (s == 0) {
+        // halo cells whose nearest interior point lies in this tile
+        T *outp = reinterpret_cast<T *>(G.out);
+        T *ppp = reinterpret_cast<T *>(G.pp);
+        for (int i = threadIdx.x; i < H * W; i += blockDim.x) {
+            const int y = i / W, x = i % W;
+            const int64_t gy = Y0 + y, gx = X0 + x;
+            if (gy < 0 || gy >= Ey || gx < 0 || gx >= Ex) continue;
+            if (gy >= R && gy < Ey - R && gx >= R && gx < Ex - R) continue;  // interior
+            const int64_t iy = min(max(gy - R, (int64_t)0), ny - 1), ix = min(max(gx - R, (int64_t)0), nx - 1);
+            if (iy / BY != tby || ix / BX != tbx) continue;
+            outp[gy * Ex + gx] = bufA[i];
+            if (ppp) ppp[gy * Ex + gx] = bufA[i];
+        }
+    }
+
+    T *src = bufA, *dst = bufB;
+    for (int sub = 1; sub <= ts; ++sub) {
+        const int lo = sub * R;
+        const int hiY = H - sub * R, hiX = W - sub * R;
+        const int cw = hiX - lo, ch = hiY - lo;
+        const int strips = (ch + V - 1) / V;
+        const bool last = sub == ts;
+        for (int item = threadIdx.x; item < cw * strips; item += blockDim.x) {
+            const int x = lo + item % cw;
+            const int y0 = lo + (item / cw) * V;
+            T acc[V];
+#pragma unroll
+            for (int j = 0; j < V; ++j) acc[j] = T(0);
+#pragma unroll
+            for (int q = 0; q < V + 2 * R; ++q) {
+                const int yy = y0 - R + q;
+                if (yy < H) {
+                    const T *row = src + yy * W + x;
+                    T v[2 * R + 1];
+#pragma unroll
+                    for (int c = 0; c < 2 * R + 1; ++c) v[c] = row[c - R];
+#pragma unroll
+                    for (int j = 0; j < V; ++j) {
+                        const int oy = q - R - j;
+                        if (oy >= -R && oy <= R) {
+#pragma unroll
+                            for (int ox = -R; ox <= R; ++ox) {
+                                const int k = cu::tap_index<SHAPE, 2, R>(0, oy, ox);
+                                if (k >= 0) acc[j] = fma(w[k], v[ox + R], acc[j]);
+                            }
+                        }
+                    }
+                }
+            }
+            const int64_t gx = X0 + x;
+            const bool colint = gx >= R && gx < Ex - R;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int y = y0 + j;
+                if (y < hiY) {
+                    const int64_t gy = Y0 + y;
+                    const bool interior = colint && gy >= R && gy < Ey - R;
+                    if (last) {
+                        if (interior) dst_g[gy * Ex + gx] = acc[j];
+                    } else {
+                        dst[y * W + x] = interior ? acc[j] : src[y * W + x];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        T *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) batch_sweeps(const GridDev *__restrict__ grids, const Item *__restrict__ items,
+                                                         int nitems, const T *__restrict__ wtab, int *done, Ctl *ctl)
+{
+    constexpr int V = sizeof(T) == 8 ? 4 : 8;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_idx, s_go;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_idx = *(volatile int *)&ctl->abort ? nitems : atomicAdd(&ctl->head, 1);
+            s_go = 1;
+        }
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= nitems) break;
+        const Item it = items[idx];
+        const GridDev G = grids[it.g];
+        if (it.s > 0 && threadIdx.x == 0) {
+            const int *dep = done + G.doff + it.s - 1;
+            const unsigned long long t0 = clock64();
+            while (ld_acquire(dep) < G.ntiles) {
+                if (clock64() - t0 > kWaitCycles || *(volatile int *)&ctl->abort) {
+                    atomicExch(&ctl->abort, 1);
+                    s_go = 0;
+                    break;
+                }
+            }
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int ts = (it.s == G.nsweeps - 1 && G.rem) ? G.rem : G.t;
+        const T *src = it.s == 0 ? reinterpret_cast<const T *>(G.in)
+                                 : reinterpret_cast<const T *>(((G.nsweeps - it.s) % 2 == 0) ? G.out : G.pp);
+        T *dst = reinterpret_cast<T *>(((G.nsweeps - 1 - it.s) % 2 == 0) ? G.out : G.pp);
+        const T *wg = wtab + G.woff;
+        switch (G.kind) {
+        case 0 * 4 + 1: run_item<T, 0, 1, V>(G, wg, src, dst, it.tile, it.s, ts, smem); break;
+        case 0 * 4 + 2: run_item<T, 0, 2, V>(G, wg, src, dst, it.tile, it.s, ts, smem); break;
+        case 0 * 4 + 3: run_item<T, 0, 3, V>(G, wg, src, dst, it.tile, it.s, ts, smem); break;
+        case 1 * 4 + 1: run_item<T, 1, 1, V>(G, wg, src, dst, it.tile, it.s, ts, smem); break;
+        case 1 * 4 + 2: run_item<T, 1, 2, V>(G, wg, src, dst, it.tile, it.s, ts, smem); break;
+        case 1 * 4 + 3: run_item<T, 1, 3, V>(G, wg, src, dst, it.tile, it.s, ts, smem); break;
+        default: break;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(done + G.doff + it.s, 1);
+    }
+}
+
+}  // namespace bt
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct BatchGridHost {
+    Plan plan;  // pattern, weights, t and tile chosen by the CUDA-core dispatch
+};
+
+struct BatchCache {
+    std::vector<const void *> ins;
+    std::vector<void *> outs;
+    int64_t steps = -1;
+    void *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+}  // namespace gbs
+
+struct stencil_batch {
+    stencil_dtype dtype = STENCIL_F32;
+    std::vector<gbs::BatchGridHost> grids;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t ctl_off = 0;  // control word of the last run
+    bool ran = false;
+    gbs::BatchCache cache;
+};
+
+namespace gbs {
+namespace {
+
+struct Layout {
+    size_t grids_off, items_off, w_off, done_off, ctl_off, pp_off, total;
+    int nitems, ndone;
+    std::vector<size_t> pp_of;  // per grid: offset of its ping-pong buffer (or SIZE_MAX)
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int sweeps_of(const Plan &p, int64_t steps) { return (int)(steps / p.t + (steps % p.t ? 1 : 0)); }
+
+int64_t ntiles_of(const Plan &p)
+{
+    return ((p.dims[1] + p.tile[1] - 1) / p.tile[1]) * ((p.dims[2] + p.tile[2] - 1) / p.tile[2]);
+}
+
+Layout layout_of(const stencil_batch &b, int64_t steps)
+{
+    Layout L{};
+    const size_t es = b.dtype == STENCIL_F64 ? 8 : 4;
+    int64_t nitems = 0, ndone = 0, nw = 0;
+    for (auto &g : b.grids) {
+        const int ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
+        nitems += ntiles_of(g.plan) * ns;
+        ndone += ns;
+        nw += g.plan.pat.K;
+    }
+    L.nitems = (int)nitems;
+    L.ndone = (int)ndone;
+    size_t off = 0;
+    L.grids_off = off;
+    off = align_up(off + sizeof(bt::GridDev) * b.grids.size(), 256);
+    L.items_off = off;
+    off = align_up(off + sizeof(bt::Item) * (size_t)nitems, 256);
+    L.w_off = off;
+    off = align_up(off + es * (size_t)nw, 256);
+    L.done_off = off;
+    off = align_up(off + sizeof(int) * (size_t)std::max<int64_t>(ndone, 1), 256);
+    L.ctl_off = off;
+    off = align_up(off + sizeof(bt::Ctl), 256);
+    L.pp_off = off;
+    for (auto &g : b.grids) {
+        const int ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
+        if (ns > 1) {
+            L.pp_of.push_back(off);
+            off = align_up(off + g.plan.grid_bytes(), 256);
+        } else {
+            L.pp_of.push_back(SIZE_MAX);
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+stencil_status launch_batch(stencil_batch *b, const Layout &L, cudaStream_t st, bool count)
+{
+    char *ws = (char *)b->ws;
+    cudaError_t e = cudaMemsetAsync(ws + L.done_off, 0, L.ctl_off - L.done_off + sizeof(bt::Ctl), st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: clearing the counters");
+    if (L.nitems == 0) return STENCIL_OK;
+    size_t smem = 0;
+    const size_t es = b->dtype == STENCIL_F64 ? 8 : 4;
+    for (auto &g : b->grids) {
+        const int R = g.plan.pat.r, t = g.plan.t;
+        smem = std::max(smem, (size_t)(g.plan.tile[1] + 2 * t * R) * (g.plan.tile[2] + 2 * t * R) * es * 2);
+    }
+    static int cached64 = 0, cached32 = 0;
+    const void *fn = b->dtype == STENCIL_F64 ? (const void *)bt::batch_sweeps<double> : (const void *)bt::batch_sweeps<float>;
+    stencil_status s = ensure_smem(fn, smem, b->dtype == STENCIL_F64 ? &cached64 : &cached32);
+    if (s != STENCIL_OK) return s;
+    int occ = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bt::kThreads, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: occupancy");
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>(L.nitems, (int64_t)std::max(1, occ) * sms);
+    const bt::GridDev *gd = (const bt::GridDev *)(ws + L.grids_off);
+    const bt::Item *items = (const bt::Item *)(ws + L.items_off);
+    int *done = (int *)(ws + L.done_off);
+    bt::Ctl *ctl = (bt::Ctl *)(ws + L.ctl_off);
+    if (b->dtype == STENCIL_F64)
+        bt::batch_sweeps<double><<<grid, bt::kThreads, smem, st>>>(gd, items, L.nitems, (const double *)(ws + L.w_off),
+                                                                   done, ctl);
+    else
+        bt::batch_sweeps<float><<<grid, bt::kThreads, smem, st>>>(gd, items, L.nitems, (const float *)(ws + L.w_off),
+                                                                  done, ctl);
+    note_launch();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "batch_sweeps launch");
+}
+
+// Host tables for one run: grid descriptors with this run's pointers, the
+// sweep-major work list and the weights, uploaded into the workspace.
+stencil_status upload_tables(stencil_batch *b, const Layout &L, const void *const *ins, void *const *outs,
+                             int64_t steps, cudaStream_t st)
+{
+    const size_t es = b->dtype == STENCIL_F64 ? 8 : 4;
+    std::vector<unsigned char> host(L.done_off, 0);
+    bt::GridDev *gd = (bt::GridDev *)(host.data() + L.grids_off);
+    bt::Item *items = (bt::Item *)(host.data() + L.items_off);
+    unsigned char *w = host.data() + L.w_off;
+    int woff = 0, doff = 0, maxs = 0;
+    for (size_t i = 0; i < b->grids.size(); i++) {
+        const Plan &p = b->grids[i].plan;
+        bt::GridDev &g = gd[i];
+        g.in = ins[i];
+        g.out = outs[i];
+        g.pp = L.pp_of[i] == SIZE_MAX ? nullptr : (char *)b->ws + L.pp_of[i];
+        g.ey = p.ext[1];
+        g.ex = p.ext[2];
+        g.kind = p.pat.shape * 4 + p.pat.r;
+        g.t = p.t;
+        g.nsweeps = sweeps_of(p, steps);
+        g.rem = (int)(steps % p.t);
+        g.by = p.tile[1];
+        g.bx = p.tile[2];
+        g.ntx = (int)((p.dims[2] + g.bx - 1) / g.bx);
+        g.ntiles = (int)ntiles_of(p);
+        g.woff = woff;
+        g.doff = doff;
+        for (int k = 0; k < p.pat.K; k++) {
+            if (es == 8) ((double *)w)[woff + k] = p.w[k];
+            else ((float *)w)[woff + k] = (float)p.w[k];
+        }
+        woff += p.pat.K;
+        doff += g.nsweeps;
+        maxs = std::max(maxs, g.nsweeps);
+    }
+    int n = 0;
+    for (int s = 0; s < maxs; s++)
+        for (size_t i = 0; i < b->grids.size(); i++)
+            if (s < gd[i].nsweeps)
+                for (int tl = 0; tl < gd[i].ntiles; tl++) items[n++] = bt::Item{(int)i, tl, s, 0};
+    cudaError_t e = cudaMemcpyAsync(b->ws, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table is released on return
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "batch: uploading the tables");
+}
+
+stencil_status check_run_args(stencil_batch *b, const void *const *ins, void *const *outs, int64_t steps,
+                              Layout *L)
+{
+    if (!b || !ins || !outs) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_run: null argument");
+    if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_run: steps < 0");
+    for (size_t i = 0; i < b->grids.size(); i++) {
+        if (!ins[i] || !outs[i] || ins[i] == outs[i])
+            return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_run: grid " + std::to_string(i) +
+                                                     ": null or identical in/out");
+    }
+    *L = layout_of(*b, steps);
+    if (!b->ws || b->ws_bytes < L->total)
+        return fail(STENCIL_ERR_OOM, "stencil_batch_run: workspace smaller than stencil_batch_workspace_bytes");
+    return STENCIL_OK;
+}
+
+void drop_graph(BatchCache &c)
+{
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c.exec = nullptr;
+    c.graph = nullptr;
+    c.steps = -1;
+}
+
+}  // namespace
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" {
+
+stencil_status stencil_batch_create(stencil_batch **batch, int n, const stencil_grid_desc *grids, stencil_dtype dtype,
+                                    int t)
+{
+    if (!batch) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_create: batch is null");
+    *batch = nullptr;
+    if (n < 1 || !grids) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_create: need n >= 1 grids");
+    if (dtype != STENCIL_F64 && dtype != STENCIL_F32)
+        return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_create: dtype must be F64 or F32");
+    if (t < 0 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_create: t must be 0..16");
+    auto *b = new (std::nothrow) stencil_batch;
+    if (!b) return fail(STENCIL_ERR_OOM, "stencil_batch_create: host allocation");
+    b->dtype = dtype;
+    for (int i = 0; i < n; i++) {
+        const stencil_grid_desc &d = grids[i];
+        if (d.r < 1 || d.r > bt::kMaxR || (d.shape != STENCIL_BOX && d.shape != STENCIL_STAR)) {
+            delete b;
+            return fail(STENCIL_ERR_UNSUPPORTED, "stencil_batch_create: grid " + std::to_string(i) +
+                                                     ": the batched form takes box/star with r = 1..3");
+        }
+        int64_t dims[2] = {d.ny, d.nx};
+        stencil_plan *p = nullptr;
+        stencil_status s = stencil_plan_create(&p, (stencil_shape)d.shape, 2, d.r, d.weights, dtype, dims, t);
+        if (s == STENCIL_OK) s = stencil_plan_set_option(p, "path", "cuda_core");
+        if (s != STENCIL_OK) {
+            stencil_plan_destroy(p);
+            delete b;
+            return s;
+        }
+        BatchGridHost g;
+        g.plan = p->p;
+        stencil_plan_destroy(p);
+        // one staging + one work buffer per item: keep the tile within ~100 KB
+        int tile[3];
+        cu_default_tile(g.plan, g.plan.t, tile);
+        for (;;) {
+            size_t bytes = (size_t)(tile[1] + 2 * g.plan.t * d.r) * (tile[2] + 2 * g.plan.t * d.r) *
+                           g.plan.elem_bytes() * 2;
+            if (bytes <= 100 * 1024 || (tile[1] <= 16 && tile[2] <= 16)) break;
+            if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
+        }
+        for (int k = 0; k < 3; k++) g.plan.tile[k] = tile[k];
+        b->grids.push_back(std::move(g));
+    }
+    *batch = b;
+    return STENCIL_OK;
+}
+
+size_t stencil_batch_workspace_bytes(const stencil_batch *batch, int64_t steps)
+{
+    if (!batch || steps < 0) return 0;
+    return layout_of(*batch, steps).total;
+}
+
+stencil_status stencil_batch_set_workspace(stencil_batch *batch, void *dev_ptr, size_t bytes)
+{
+    if (!batch) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_workspace: batch is null");
+    if (!dev_ptr && bytes) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_workspace: null with bytes > 0");
+    if (dev_ptr != batch->ws) drop_graph(batch->cache);
+    batch->ws = dev_ptr;
+    batch->ws_bytes = dev_ptr ? bytes : 0;
+    return STENCIL_OK;
+}
+
+stencil_status stencil_batch_info(const stencil_batch *batch, int i, stencil_info *info)
+{
+    if (!batch || !info || i < 0 || i >= (int)batch->grids.size())
+        return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_info: bad argument");
+    *info = batch->grids[i].plan.info;
+    for (int k = 0; k < 3; k++) info->tile[k] = batch->grids[i].plan.tile[k];
+    return STENCIL_OK;
+}
+
+stencil_status stencil_batch_run(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
+                                 stencil_stream_t stream)
+{
+    Layout L;
+    stencil_status s = check_run_args(batch, ins, outs, steps, &L);
+    if (s != STENCIL_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (steps == 0) {
+        for (size_t i = 0; i < batch->grids.size(); i++) {
+            cudaError_t e = cudaMemcpyAsync(outs[i], ins[i], batch->grids[i].plan.grid_bytes(),
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run: copy");
+        }
+        return STENCIL_OK;
+    }
+    drop_graph(batch->cache);  // the tables are about to change
+    s = upload_tables(batch, L, ins, outs, steps, st);
+    if (s != STENCIL_OK) return s;
+    return launch_batch(batch, L, st, true);
+}
+
+stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
+                                       stencil_stream_t stream)
+{
+    Layout L;
+    stencil_status s = check_run_args(batch, ins, outs, steps, &L);
+    if (s != STENCIL_OK) return s;
+    if (!stream) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_run_graph: needs a non-default stream");
+    if (steps == 0) return stencil_batch_run(batch, ins, outs, 0, stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchCache &c = batch->cache;
+    const size_t n = batch->grids.size();
+    const bool same = c.exec && c.steps == steps && c.ws == batch->ws && c.stream == st &&
+                      std::equal(c.ins.begin(), c.ins.end(), ins) && std::equal(c.outs.begin(), c.outs.end(), outs);
+    if (!same) {
+        drop_graph(c);
+        s = upload_tables(batch, L, ins, outs, steps, st);
+        if (s != STENCIL_OK) return s;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run_graph: begin capture");
+        s = launch_batch(batch, L, st, false);  // counted at each replay
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (s != STENCIL_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run_graph: end capture");
+        e = cudaGraphInstantiate(&c.exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "stencil_batch_run_graph: instantiate");
+        }
+        c.graph = g;
+        c.ins.assign(ins, ins + n);
+        c.outs.assign(outs, outs + n);
+        c.steps = steps;
+        c.ws = batch->ws;
+        c.stream = st;
+    }
+    cudaError_t e = cudaGraphLaunch(c.exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run_graph: launch");
+    note_launch();
+    return STENCIL_OK;
+}
+
+stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t stream)
+{
+    if (!batch) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_status: batch is null");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_status: stream");
+    if (!batch->ran || !batch->ws) return STENCIL_OK;
+    bt::Ctl ctl{};
+    e = cudaMemcpy(&ctl, (char *)batch->ws + batch->ctl_off, sizeof(ctl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_status: reading the control word");
+    if (ctl.abort) return fail(STENCIL_ERR_TIMEOUT, "stencil_batch: a dependency wait ran out; outputs incomplete");
+    return STENCIL_OK;
+}
+
+void stencil_batch_destroy(stencil_batch *batch)
+{
+    if (!batch) return;
+    drop_graph(batch->cache);
+    delete batch;
+}
+
+}  // extern "C"

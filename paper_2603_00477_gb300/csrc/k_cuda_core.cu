@@ -26,43 +26,70 @@ stencil_status ensure_smem(const void *func, size_t bytes, int *cached)
 
 namespace {
 
-constexpr int kV = 8;
+template <typename T>
+constexpr int kV = sizeof(T) == 8 ? 4 : 8;  // strip height: FP64 needs fewer accumulators
 constexpr size_t kMaxSmem = 227 * 1024;
+
+// Band ring: tiles that contain a point closer than `band` to the interior
+// boundary.  Along y these are the tile rows below ceil(band/BY) and from
+// floor((ny-band)/BY) on (the last tile row may be partial), likewise in x.
+cu::Ring make_ring(int64_t ny, int64_t nx, int BY, int BX, int band)
+{
+    cu::Ring g{};
+    g.nty = (int)((ny + BY - 1) / BY);
+    g.ntx = (int)((nx + BX - 1) / BX);
+    g.band = band;
+    if (band <= 0) return g;
+    const int top = (int)std::min<int64_t>(g.nty, (band + BY - 1) / BY);
+    const int bot = g.nty - (int)(std::max<int64_t>(0, ny - band) / BY);
+    const int left = (int)std::min<int64_t>(g.ntx, (band + BX - 1) / BX);
+    const int right = g.ntx - (int)(std::max<int64_t>(0, nx - band) / BX);
+    g.top_w = top;
+    g.rows_tb = std::min(g.nty, top + bot);
+    g.left_w = left;
+    g.cols_lr = std::min(g.ntx, left + right);
+    return g;
+}
+
+int64_t ring_count(const cu::Ring &g)
+{
+    if (g.band <= 0) return (int64_t)g.nty * g.ntx;
+    return (int64_t)g.rows_tb * g.ntx + (int64_t)(g.nty - g.rows_tb) * g.cols_lr;
+}
 
 template <typename T, int SHAPE, int R>
 stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
 {
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 2, R>::K>;
     static int cached = 0;
+    static int occ_smem = -1, occ_blocks = 0;
     Wt wt;
     for (int k = 0; k < cu::Taps<SHAPE, 2, R>::K; k++) wt.w[k] = (T)p.w[k];
     int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
     if (band > 0 || p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
     const int BY = tile[1], BX = tile[2];
     const size_t H = BY + 2 * t * R, W = BX + 2 * t * R;
-    const size_t smem = H * W * sizeof(T) * (t > 1 ? 2 : 1);
+    // weights (FP64) + two staging buffers (+ a work buffer for t > 1)
+    const size_t smem = cu::weight_smem_bytes<T, cu::Taps<SHAPE, 2, R>::K>() + H * W * sizeof(T) * (t > 1 ? 3 : 2);
     if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
-    auto kern = cu::cu2d_sweep<T, SHAPE, R, kV>;
+    auto kern = cu::cu2d_sweep<T, SHAPE, R, kV<T>>;
     stencil_status s = ensure_smem((const void *)kern, smem, &cached);
     if (s != STENCIL_OK) return s;
-    const int64_t ny = p.dims[1], nx = p.dims[2];
-    const int nty = (int)((ny + BY - 1) / BY), ntx = (int)((nx + BX - 1) / BX);
-    cu::Ring ring{};
-    dim3 grid((unsigned)ntx, (unsigned)nty);
-    if (band > 0) {
-        ring.band = band;
-        ring.nty = nty;
-        ring.ntx = ntx;
-        ring.by_w = std::min(nty, (band + BY - 1) / BY);
-        ring.bx_w = std::min(ntx, (band + BX - 1) / BX);
-        ring.rows_tb = std::min(nty, 2 * ring.by_w);
-        ring.cols_lr = std::min(ntx, 2 * ring.bx_w);
-        const int64_t count = (int64_t)ring.rows_tb * ntx + (int64_t)(nty - ring.rows_tb) * ring.cols_lr;
-        grid = dim3((unsigned)count, 1);
-    } else if (grid.y > 65535) {
-        return fail(STENCIL_ERR_UNSUPPORTED, "grid too tall for the tile");
+    if (occ_smem != (int)smem) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        occ_smem = (int)smem;
     }
-    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[1], p.ext[2], BY, BX, t, ring);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const cu::Ring ring = make_ring(p.dims[1], p.dims[2], BY, BX, band);
+    const int64_t ntiles = ring_count(ring);
+    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, resident);
+    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[1], p.ext[2], BY, BX, t, ring,
+                                           (int)ntiles);
     note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu2d_sweep launch");
@@ -73,21 +100,35 @@ stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStr
 {
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
     static int cached = 0;
+    static int occ_smem = -1, occ_blocks = 0;
     Wt wt;
     for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];
-    const int BZ = p.tile[0], BY = p.tile[1], BX = p.tile[2];
+    int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
+    if (p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
+    const int BZ = tile[0], BY = tile[1], BX = tile[2];
     const size_t Z = BZ + 2 * t * R, H = BY + 2 * t * R, W = BX + 2 * t * R;
-    const size_t smem = Z * H * W * sizeof(T) * (t > 1 ? 2 : 1);
+    const size_t smem =
+        cu::weight_smem_bytes<T, cu::Taps<SHAPE, 3, R>::K>() + Z * H * W * sizeof(T) * (t > 1 ? 3 : 2);
     if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
-    auto kern = cu::cu3d_sweep<T, SHAPE, R, kV>;
+    auto kern = cu::cu3d_sweep<T, SHAPE, R, kV<T>>;
     stencil_status s = ensure_smem((const void *)kern, smem, &cached);
     if (s != STENCIL_OK) return s;
+    if (occ_smem != (int)smem) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        occ_smem = (int)smem;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t nz = p.dims[0], ny = p.dims[1], nx = p.dims[2];
     const int64_t tx = (nx + BX - 1) / BX, ty = (ny + BY - 1) / BY, tz = (nz + BZ - 1) / BZ;
-    if (tx * ty > 0x7fffffff || tz > 65535) return fail(STENCIL_ERR_UNSUPPORTED, "grid too large for the tile");
-    dim3 grid((unsigned)(tx * ty), (unsigned)tz);
+    const int64_t ntiles = tx * ty * tz;
+    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, resident);
     kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[0], p.ext[1], p.ext[2], BZ, BY, BX,
-                                           t, (int)tx);
+                                           t, (int)tx, (int)ty, (int)ntiles);
     note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu3d_sweep launch");

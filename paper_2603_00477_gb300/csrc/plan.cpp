@@ -53,11 +53,12 @@ void cu_default_tile(const Plan &p, int t, int tile[3])
         tile[0] = 1;
         tile[1] = 64;
         tile[2] = p.dtype == STENCIL_F64 ? 64 : 128;
-        // keep two smem buffers under ~200 KB
+        // two staging buffers (+ a work buffer for t > 1) under ~112 KB, so
+        // that two CTAs share an SM
         for (;;) {
             size_t h = tile[1] + 2 * t * R, w = tile[2] + 2 * t * R;
-            size_t bytes = h * w * p.elem_bytes() * (t > 1 ? 2 : 1);
-            if (bytes <= 200 * 1024 || tile[2] <= 32) break;
+            size_t bytes = h * w * p.elem_bytes() * (t > 1 ? 3 : 2);
+            if (bytes <= 112 * 1024 || (tile[2] <= 16 && tile[1] <= 16)) break;
             if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
         }
     } else {
@@ -66,9 +67,11 @@ void cu_default_tile(const Plan &p, int t, int tile[3])
         tile[2] = 32;
         for (;;) {
             size_t z = tile[0] + 2 * t * R, h = tile[1] + 2 * t * R, w = tile[2] + 2 * t * R;
-            size_t bytes = z * h * w * p.elem_bytes() * (t > 1 ? 2 : 1);
-            if (bytes <= 200 * 1024 || tile[0] <= 2) break;
-            tile[0] /= 2;
+            size_t bytes = z * h * w * p.elem_bytes() * (t > 1 ? 3 : 2);
+            if (bytes <= 112 * 1024 || (tile[0] <= 2 && tile[1] <= 4 && tile[2] <= 8)) break;
+            if (tile[0] > 2) tile[0] /= 2;
+            else if (tile[1] > 4) tile[1] /= 2;
+            else tile[2] /= 2;
         }
     }
 }

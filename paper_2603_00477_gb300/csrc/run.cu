@@ -154,3 +154,4 @@ extern "C" stencil_status stencil_device_status(stencil_stream_t stream)
     if (flag) return fail(STENCIL_ERR_TIMEOUT, "a tensor-core kernel's bounded wait for its MMAs ran out");
     return STENCIL_OK;
 }
+

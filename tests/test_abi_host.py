@@ -192,3 +192,36 @@ def test_dispatch_fp32_fuses_until_compute_bound(lib):
         assert info["path"] == B.PATH_CUDA_CORE and info["t"] >= 2
     finally:
         B.stencil_plan_destroy(p)
+
+
+# ---- batched form (host side) ---------------------------------------------------------
+
+def test_batch_create_validation(lib):
+    w9 = _w("box", 2, 1)
+    with pytest.raises(B.StencilError) as e:
+        B.stencil_batch_create([], "f32")
+    assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+    with pytest.raises(B.StencilError) as e:
+        B.stencil_batch_create([("box", 4, 10, 10, _w("box", 2, 4))], "f32")
+    assert e.value.status == B.STENCIL_ERR_UNSUPPORTED
+    with pytest.raises(B.StencilError) as e:
+        B.stencil_batch_create([("box", 1, 0, 10, w9)], "f32")
+    assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+
+
+def test_batch_workspace_and_no_launch_without_it(lib):
+    grids = [("box", 1, 100, 120, _w("box", 2, 1)), ("star", 2, 33, 7, _w("star", 2, 2))]
+    h = B.stencil_batch_create(grids, "f32", 2)
+    try:
+        one = B.stencil_batch_workspace_bytes(h, 2)   # one sweep each: no ping-pong grids
+        many = B.stencil_batch_workspace_bytes(h, 9)
+        assert many > one > 0
+        assert many - one >= (102 * 122 + 37 * 11) * 4  # a ping-pong grid per grid
+        assert B.stencil_batch_info(h, 0)["t"] == 2
+        n0 = B.stencil_launch_count()
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_batch_run(h, [4096, 8192], [1 << 20, 1 << 21], 9, 0)
+        assert e.value.status == B.STENCIL_ERR_OOM
+        assert B.stencil_launch_count() == n0
+    finally:
+        B.stencil_batch_destroy(h)
