@@ -214,6 +214,24 @@ stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *h
 stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_tc_layout *layout, int *kb_lo,
                                       int *kb_hi, double *B);
 
+/* stencil_run without any device allocation, for callers that may not call
+ * cudaMalloc (e.g. a plugin inside an application that owns all device memory
+ * through its own allocator, or a loop that cannot take the implicit
+ * synchronisation an allocation may bring).  The paper has no counterpart;
+ * this is a library service.  Same computation and arguments as stencil_run,
+ * but the ping-pong buffer between fused sweeps is a 64 MiB static device
+ * array of this library instead of the plan's workspace (each GPU that loads
+ * the library holds it until the process exits).  Grids whose stored size
+ * (halo included) exceeds 64 MiB are rejected with STENCIL_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and it keeps the previous call's
+ * contents (nothing in it needs to start at zero: every cell a sweep reads is
+ * written earlier in the same call); calls that overlap on the GPU, from any
+ * stream or thread, race on it. */
+stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in, void *out, int64_t steps,
+                                   stencil_stream_t stream);
+
 /* Release a plan (never frees caller workspace).  Null is ignored. */
 void stencil_plan_destroy(stencil_plan *plan);
 

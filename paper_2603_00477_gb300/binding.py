@@ -100,6 +100,8 @@ def load() -> ctypes.CDLL:
     L.stencil_plan_set_workspace.restype = st
     L.stencil_run.argtypes = [vp, vp, vp, i64, vp]
     L.stencil_run.restype = st
+    L.stencil_run_noalloc.argtypes = [vp, vp, vp, i64, vp]
+    L.stencil_run_noalloc.restype = st
     L.stencil_run_host.argtypes = [vp, vp, vp, i64, vp]
     L.stencil_run_host.restype = st
     L.stencil_plan_destroy.argtypes = [vp]
@@ -210,6 +212,11 @@ def stencil_plan_set_workspace(plan: int, dev_ptr: int, nbytes: int) -> None:
 
 def stencil_run(plan: int, in_ptr: int, out_ptr: int, steps: int, stream=None) -> None:
     _check(load().stencil_run(plan, in_ptr, out_ptr, int(steps), _stream_handle(stream)), "stencil_run")
+
+
+def stencil_run_noalloc(plan: int, in_ptr: int, out_ptr: int, steps: int, stream=None) -> None:
+    _check(load().stencil_run_noalloc(plan, in_ptr, out_ptr, int(steps), _stream_handle(stream)),
+           "stencil_run_noalloc")
 
 
 def stencil_run_host(plan: int, host_in_ptr: int, host_out_ptr: int, steps: int, stream=None) -> None:

@@ -155,3 +155,73 @@ extern "C" stencil_status stencil_device_status(stencil_stream_t stream)
     return STENCIL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// stencil_run_noalloc: the multi-sweep run without any device allocation.
+//
+// Some callers cannot call cudaMalloc: code embedded in a host application
+// that owns all device memory through its own allocator and forbids direct
+// CUDA allocations, or a latency-critical loop that cannot afford the
+// implicit device synchronisation an allocation may cause.  For them the
+// ping-pong buffer between fused sweeps lives in a fixed, statically sized
+// device array of this library (every GPU that loads the library keeps it
+// until the process exits).  The caller still passes `in` and `out`.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gbs {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;  // 64 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+// In host code this name is only a host-side stand-in for the device array;
+// kernels get the device address obtained from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices];
+
+// Set-up, once per device, with that device current: the device address of
+// the scratch array.
+stencil_status noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_run_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(STENCIL_ERR_UNSUPPORTED, "stencil_run_noalloc: device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "stencil_run_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return STENCIL_OK;
+}
+
+}  // namespace
+}  // namespace gbs
+
+extern "C" stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in, void *out, int64_t steps,
+                                              stencil_stream_t stream)
+{
+    if (!plan || !in || !out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: null argument");
+    if (in == out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: in and out must differ");
+    if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: steps < 0");
+    Plan &p = plan->p;
+    const size_t g = p.grid_bytes();
+    {
+        const char *b = (const char *)in, *c = (const char *)out;
+        if (b < c + g && c < b + g) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: in and out overlap");
+    }
+    if (g > kNoAllocScratchBytes)
+        return fail(STENCIL_ERR_UNSUPPORTED, "stencil_run_noalloc: the grid (" + std::to_string(g) +
+                                                 " bytes with halo) exceeds the 64 MiB static scratch; "
+                                                 "use stencil_run with a workspace");
+    void *scratch = nullptr;
+    stencil_status s = noalloc_scratch(&scratch);
+    if (s != STENCIL_OK) return s;
+    return run_sweeps(p, in, out, scratch, kNoAllocScratchBytes, steps, (cudaStream_t)stream);
+}
