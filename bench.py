@@ -155,12 +155,10 @@ def cpu_baseline(cfg, w, u, budget_s=15.0):
     import oracle
     u64 = np.ascontiguousarray(u, dtype=np.float64)
     d = cfg["d"]
-    probe_dims = (256,) * d if d == 2 else (48,) * d
-    small = np.ascontiguousarray(u64[tuple(slice(0, n + 2 * cfg["r"]) for n in probe_dims)])
     t0 = time.perf_counter()
-    oracle.run(cfg["shape"], d, cfg["r"], w, probe_dims, small, 1)
-    per_point = (time.perf_counter() - t0) / math.prod(probe_dims)
-    steps = max(1, min(cfg["steps"], int(budget_s / max(per_point * points_of(cfg), 1e-9))))
+    oracle.run(cfg["shape"], d, cfg["r"], w, cfg["dims"], u64, 1)  # calibration: one step of the full grid
+    one = time.perf_counter() - t0
+    steps = max(1, min(cfg["steps"], int(budget_s / max(one, 1e-9))))
     t0 = time.perf_counter()
     oracle.run(cfg["shape"], d, cfg["r"], w, cfg["dims"], u64, steps)
     el = time.perf_counter() - t0
@@ -229,6 +227,104 @@ def traffic_record(kernel_key):
     return float(rec["dram_bytes_per_launch"])
 
 
+
+def _time_runs(fn, stream, reps=3, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def mixed_precision_leg(B, inputs, stream, steps=100):
+    """Box-2D2R FP32 16384^2 (sine-mode field): plain FP32 on CUDA cores at the
+    model's t against the tensor-core TF32, TF32x3 and BF16x3 forms at each
+    t = 1..4 (point-updates/s; errors are checked in the GPU tests)."""
+    import numpy as np
+    import torch
+    dims = (16384, 16384)
+    w, u = inputs.problem("box", 2, 2, dims, seed=4, dtype=np.float32, field="sine")
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    pts = dims[0] * dims[1]
+    rows = []
+    cands = [("cuda_core", "native", t) for t in (1, 2, 3, 4)] + \
+            [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3") for t in (1, 2, 3, 4)]
+    for path, prec, t in cands:
+        plan = B.Plan("box", 2, 2, w, "f32", dims, t)
+        if prec != "native":
+            plan.set_option("precision", prec)
+        plan.set_option("path", path)
+        plan.ensure_workspace(x.device)
+        sec = _time_runs(lambda: plan.run(x, y, steps), stream)
+        info = plan.info()
+        rows.append({"path": path, "precision": prec, "t": t, "gstencils": pts * steps / sec / 1e9,
+                     "model_gstencils": info["predicted_gstencils"], "alpha": info["alpha"],
+                     "sparsity": info["sparsity"], "beta": info["beta"]})
+        plan.close()
+    del x, y
+    torch.cuda.empty_cache()
+    plain = max(r["gstencils"] for r in rows if r["path"] == "cuda_core")
+    best = max(rows, key=lambda r: r["gstencils"])
+    return {"workload": f"Box-2D2R F32 16384x16384, sine-mode field, {steps} steps per run",
+            "plain_fp32_cuda_core_gstencils": plain, "best": best, "rows": rows}
+
+
+def batched_leg(B, inputs, stream, steps=20):
+    """512 uneven FP32 grids, 4 stencil kinds: one persistent launch replayed
+    from a CUDA graph against a per-grid loop of plain stencil_run calls."""
+    import numpy as np
+    import torch
+    descs = inputs.batch_descs()
+    probs = []
+    for (shape, r, ny, nx, seed) in descs:
+        w = inputs.weights(shape, 2, r, seed)
+        probs.append((shape, r, ny, nx, w))
+    # fields: one seeded U(0,1) draw per grid (interior), zero halo
+    ins, outs = [], []
+    for i, (shape, r, ny, nx, w) in enumerate(probs):
+        u = inputs.uniform_field((ny, nx), r, descs[i][4], len(w), np.float32)
+        ins.append(torch.from_numpy(u).cuda())
+        outs.append(torch.empty_like(ins[-1]))
+    pts = sum(ny * nx for (_, _, ny, nx, _) in probs)
+    batch = B.Batch(probs, "f32", 0)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        sec_graph = _time_runs(lambda: batch.run(ins, outs, steps, stream=side, graph=True), side)
+        sec_batch = _time_runs(lambda: batch.run(ins, outs, steps, stream=side, graph=False), side)
+    plans = [B.Plan(s, 2, r, w, "f32", (ny, nx), 0) for (s, r, ny, nx, w) in probs]
+    for p in plans:
+        p.set_option("path", "cuda_core")
+        p.ensure_workspace(ins[0].device)
+
+    def loop():
+        for p, a, b in zip(plans, ins, outs):
+            p.run(a, b, steps)
+    n0 = B.stencil_launch_count()
+    loop()
+    torch.cuda.synchronize()
+    loop_launches = B.stencil_launch_count() - n0
+    sec_loop = _time_runs(loop, stream, reps=2)
+    for p in plans:
+        p.close()
+    batch.close()
+    del ins, outs
+    torch.cuda.empty_cache()
+    return {"workload": f"512 FP32 grids, sides log-uniform in [64, 4096], Star-2D1R/Star-2D2R/Box-2D1R/Box-2D3R, "
+                        f"{steps} steps, {pts} interior points",
+            "persistent_graph_gstencils": pts * steps / sec_graph / 1e9,
+            "persistent_gstencils": pts * steps / sec_batch / 1e9,
+            "per_grid_loop_gstencils": pts * steps / sec_loop / 1e9,
+            "per_grid_loop_launches": loop_launches, "persistent_launches": 1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -242,6 +338,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-(path, t) sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and batched legs")
     ap.add_argument("--dims", default=None, help="override the interior extents (profiling), e.g. 6144,6144")
     ap.add_argument("--run-steps", type=int, default=None, help="override the steps per run (profiling)")
     args = ap.parse_args()
@@ -287,10 +384,10 @@ def main():
         oracle.build()
         cpu = cpu_baseline(cfg, w, u)
     plan = B.Plan(cfg["shape"], cfg["d"], cfg["r"], w, cfg["dtype"], cfg["dims"], args.t)
-    if args.path != "auto":
-        plan.set_option("path", args.path)
     if args.precision:
         plan.set_option("precision", args.precision)
+    if args.path != "auto":
+        plan.set_option("path", args.path)
     info = plan.info()
     x = torch.from_numpy(u).cuda()
     y = torch.empty_like(x)
@@ -410,6 +507,15 @@ def main():
                 p2._ws = None
                 p2.close()
 
+    extras = {}
+    if not args.no_extras and rank == 0 and args.config == DEFAULT and not args.dims:
+        del x, y
+        plan._ws = None
+        torch.cuda.empty_cache()
+        extras["mixed_precision"] = mixed_precision_leg(B, inputs, stream)
+        extras["batched"] = batched_leg(B, inputs, stream)
+        extras["plain_fp64_gstencils"] = value / world
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": cfg["dtype"],
@@ -423,6 +529,7 @@ def main():
                       "intensity": info["intensity"], "ridge": info["ridge"],
                       "memory_bound": bool(info["memory_bound"])},
             "sweep": sweep}
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -171,6 +171,9 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
  *   "precision" native | tf32 | tf32x3 | bf16x3 | any
  *   "t"         0 (model) or 1..16
  *   "tile"      "TYxTX" (2-D) or "TZxTYxTX" (3-D) output tile, "0" = default
+ *   "debug_unmet_wait"  0 | 1: test hook; 1 makes every tensor-core CTA first
+ *               wait ~2 ms on an mbarrier phase that never completes, take the
+ *               timeout path (error word set, tile not written) and return
  * INVALID_ARG for an unknown key or value, UNSUPPORTED if the requested
  * path/precision has no kernel for this plan (the plan is then unchanged). */
 stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, const char *value);
@@ -284,6 +287,14 @@ stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *
 /* Synchronise `stream` and report STENCIL_ERR_TIMEOUT if the last run gave
  * up a dependency wait (its outputs are then incomplete). */
 stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t stream);
+
+/* Batch options (integer values):
+ *   "wait_cycles"        limit of each dependency wait in SM clock cycles
+ *                        (default 2^31, about one second)
+ *   "debug_block_sweep"  test hook: items of this sweep (>= 1) wait on a
+ *                        counter nothing increments, so the wait runs out and
+ *                        the launch aborts; -1 switches it off (default). */
+stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, const char *value);
 
 void stencil_batch_destroy(stencil_batch *batch);
 

@@ -135,6 +135,8 @@ def load() -> ctypes.CDLL:
     L.stencil_batch_run_graph.restype = st
     L.stencil_batch_status.argtypes = [vp, vp]
     L.stencil_batch_status.restype = st
+    L.stencil_batch_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
+    L.stencil_batch_set_option.restype = st
     L.stencil_batch_destroy.argtypes = [vp]
     L.stencil_batch_destroy.restype = None
     L.stencil_status_string.argtypes = [ctypes.c_int]
@@ -416,6 +418,11 @@ def stencil_batch_run_graph(batch: int, in_ptrs, out_ptrs, steps: int, stream=No
 
 def stencil_batch_status(batch: int, stream=None) -> None:
     _check(load().stencil_batch_status(batch, _stream_handle(stream)), "stencil_batch_status")
+
+
+def stencil_batch_set_option(batch: int, key: str, value) -> None:
+    _check(load().stencil_batch_set_option(batch, key.encode(), str(value).encode()),
+           f"stencil_batch_set_option({key})")
 
 
 def stencil_batch_destroy(batch: int) -> None:

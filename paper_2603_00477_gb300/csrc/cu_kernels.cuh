@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -117,6 +118,129 @@ __device__ __forceinline__ void cp_async_wait_group()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// FP32 sub-step, register-rotation form.  A work item is a pair of adjacent
+// columns (x, x+1) and a strip of S output rows.  The thread walks down the
+// strip's input rows once; each row window is read with 8-byte shared loads
+// (D = parity of the window start) and added to the 2R+1 output rows it
+// touches, whose partial sums rotate through 2R+1 register slots.  The row
+// loop is unrolled by 2R+1, so every slot index and weight index is a
+// compile-time constant and no FMA carries a condition; output row jj is
+// complete after input row jj + 2R and is stored from its slot.  When the
+// whole region is interior the stores skip the boundary tests.
+template <int SHAPE, int R, int D, typename WT>
+__device__ __forceinline__ void f32_substep(const float *__restrict__ src, float *__restrict__ dst,
+                                            float *__restrict__ out, const WT &wt, int W, int H, int lo, int hiY,
+                                            int hiX, int64_t Y0, int64_t X0, int64_t Ey, int64_t Ex, bool last,
+                                            bool all_interior, int band)
+{
+    constexpr int NS = 2 * R + 1;      // rotating slots
+    constexpr int NV = 2 * R + 2 + D;  // window values per row
+    constexpr int NL = (NV + 1) / 2;   // float2 loads per row
+    const int cw = hiX - lo, ch = hiY - lo;
+    const int npairs = (cw + 1) / 2;
+    // strips of ~16 rows (the 2R extra input rows per strip are the only
+    // redundant work), enough of them to give every thread work
+    const int nstrips = max(1, min((ch + 15) / 16, (int)((blockDim.x + npairs - 1) / npairs)));
+    const int S = (ch + nstrips - 1) / nstrips;
+    const int64_t ny = Ey - 2 * R, nx = Ex - 2 * R;
+
+    const bool fast = all_interior && band == 0;
+    auto store = [&](int y, int x, float v0, float v1, bool second) {
+        if (fast) {
+            if (last) {
+                float *o = out + (Y0 + y) * Ex + (X0 + x);
+                if (second && ((reinterpret_cast<uintptr_t>(o) & 7) == 0)) {
+                    *reinterpret_cast<float2 *>(o) = make_float2(v0, v1);
+                } else {
+                    o[0] = v0;
+                    if (second) o[1] = v1;
+                }
+            } else {
+                // W is even, so dst + y*W + x is 8-byte aligned exactly when x is
+                // even (x has the parity of s*R: uniform over the sub-step)
+                float *o = dst + y * W + x;
+                if (second && (x & 1) == 0) {
+                    *reinterpret_cast<float2 *>(o) = make_float2(v0, v1);
+                } else {
+                    o[0] = v0;
+                    if (second) o[1] = v1;
+                }
+            }
+            return;
+        }
+        const int64_t gy = Y0 + y, gx = X0 + x;
+        const bool rowint = gy >= R && gy < Ey - R;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !second) break;
+            const int64_t gxh = gx + h;
+            const bool interior = rowint && gxh >= R && gxh < Ex - R;
+            const float val = h ? v1 : v0;
+            if (last) {
+                bool keep = interior;
+                if (band > 0) {
+                    const int64_t iy = gy - R, ix = gxh - R;
+                    keep = keep && (iy < band || ix < band || ny - 1 - iy < band || nx - 1 - ix < band);
+                }
+                if (keep) out[gy * Ex + gxh] = val;
+            } else {
+                dst[y * W + x + h] = interior ? val : src[y * W + x + h];
+            }
+        }
+    };
+
+    for (int item = threadIdx.x; item < nstrips * npairs; item += blockDim.x) {
+        const int sy = item / npairs, px = item - sy * npairs;
+        const int y0 = lo + sy * S;
+        const int yend = min(y0 + S, hiY);  // outputs y0 .. yend-1
+        if (y0 >= yend) continue;
+        const int x = lo + 2 * px;
+        const bool second = x + 1 < hiX;
+        const int nrows = (yend - y0) + 2 * R;  // input rows y0-R .. yend-1+R
+        float a0[NS], a1[NS];
+#pragma unroll
+        for (int m = 0; m < NS; ++m) a0[m] = a1[m] = 0.0f;
+        const float *col = src + x - R - D;
+        for (int base = 0; base < nrows; base += NS) {
+#pragma unroll
+            for (int u = 0; u < NS; ++u) {
+                const int qq = base + u;  // relative input row; absolute row y0 - R + qq
+                if (qq < nrows) {
+                    const float2 *row = reinterpret_cast<const float2 *>(col + (y0 - R + qq) * W);
+                    float v[2 * NL];
+#pragma unroll
+                    for (int c = 0; c < NL; ++c) {
+                        const float2 t2 = row[c];
+                        v[2 * c] = t2.x;
+                        v[2 * c + 1] = t2.y;
+                    }
+                    // output jj = qq - e (e = 0..2R) takes this row with oy = e - R
+#pragma unroll
+                    for (int e = 0; e < NS; ++e) {
+                        const int slot = ((u - e) % NS + NS) % NS;
+#pragma unroll
+                        for (int ox = -R; ox <= R; ++ox) {
+                            const int k = tap_index<SHAPE, 2, R>(0, e - R, ox);
+                            if (k >= 0) {
+                                a0[slot] = fmaf(wt.w[k], v[D + R + ox], a0[slot]);
+                                a1[slot] = fmaf(wt.w[k], v[D + R + ox + 1], a1[slot]);
+                            }
+                        }
+                    }
+                    // output jj = qq - 2R is complete (slot (u - 2R) mod NS = (u + 1) mod NS)
+                    constexpr int dummy = 0;
+                    (void)dummy;
+                    const int jj = qq - 2 * R;
+                    const int done = (u + 1) % NS;
+                    if (jj >= 0) store(y0 + jj, x, a0[done], a1[done], second);
+                    a0[done] = 0.0f;
+                    a1[done] = 0.0f;
+                }
+            }
+        }
+    }
+}
+
 // Persistent form: CTA b processes tiles b, b + gridDim.x, ...; while it
 // computes one tile it prefetches the next into the other staging buffer
 // with cp.async, so the FMA pipe never waits for a synchronous load phase.
@@ -168,6 +292,16 @@ __global__ void __launch_bounds__(kThreads, 2)
     auto prefetch = [&](int id, T *dst) {
         int64_t Y0, X0;
         origin(id, &Y0, &X0);
+        if (Y0 >= 0 && X0 >= 0 && Y0 + H <= Ey && X0 + W <= Ex) {
+            // the whole region lies in the stored array: no per-element tests
+            const T *g = in + Y0 * Ex + X0;
+            for (int y = warp; y < H; y += nwarps) {
+                const T *grow = g + y * Ex;
+                T *srow = dst + y * W;
+                for (int x = lane; x < W; x += 32) cp_async_elem<sizeof(T)>(srow + x, grow + x, true);
+            }
+            return;
+        }
         for (int y = warp; y < H; y += nwarps) {
             const int64_t gy = Y0 + y;
             const bool rowok = gy >= 0 && gy < Ey;
@@ -198,6 +332,20 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int cw = hiX - lo, ch = hiY - lo;
             const int strips = (ch + V - 1) / V;
             const bool last = s == t;
+            if constexpr (sizeof(T) == 4) {
+                const bool all_int = Y0 + lo >= R && Y0 + hiY <= Ey - R && X0 + lo >= R && X0 + hiX <= Ex - R;
+                if (((lo - R) & 1) == 0)
+                    f32_substep<SHAPE, R, 0>(src, dst, out, wt, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
+                                             ring.band);
+                else
+                    f32_substep<SHAPE, R, 1>(src, dst, out, wt, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
+                                             ring.band);
+                __syncthreads();
+                T *tmp = src;
+                src = dst;
+                dst = tmp;
+                continue;
+            }
             for (int item = threadIdx.x; item < cw * strips; item += blockDim.x) {
                 const int x = lo + item % cw;
                 const int y0 = lo + (item / cw) * V;

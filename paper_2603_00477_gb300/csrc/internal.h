@@ -68,6 +68,7 @@ struct Plan {
     int req_precision = STENCIL_PREC_NATIVE;
     int req_t = 0;
     int req_tile[3] = {0, 0, 0};
+    int debug_unmet_wait = 0;  // test hook for the tensor-core kernels' bounded wait
 
     // decision
     int path = STENCIL_PATH_CUDA_CORE;

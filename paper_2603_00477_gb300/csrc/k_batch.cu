@@ -14,6 +14,7 @@
 // nearest to their tile from `in` to the grid's output and ping-pong buffers.
 // On a wait that runs out, the CTA sets the abort word and every CTA leaves.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -48,6 +49,8 @@ struct Item {
 struct Ctl {
     int head;   // next work item
     int abort;  // set when a dependency wait ran out
+    int never;  // a counter nothing increments (test hook: an unmet dependency)
+    int pad;
 };
 
 constexpr unsigned long long kWaitCycles = 2ull << 30;  // ~1 s at 2 GHz
@@ -116,6 +119,25 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
         const int cw = hiX - lo, ch = hiY - lo;
         const int strips = (ch + V - 1) / V;
         const bool last = sub == ts;
+        if constexpr (sizeof(T) == 4) {
+            struct {
+                float w[KT];
+            } wrs;
+#pragma unroll
+            for (int k = 0; k < KT; ++k) wrs.w[k] = w[k];
+            const bool all_int = Y0 + lo >= R && Y0 + hiY <= Ey - R && X0 + lo >= R && X0 + hiX <= Ex - R;
+            if (((lo - R) & 1) == 0)
+                cu::f32_substep<SHAPE, R, 0>(src, dst, dst_g, wrs, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last,
+                                                all_int, 0);
+            else
+                cu::f32_substep<SHAPE, R, 1>(src, dst, dst_g, wrs, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last,
+                                                all_int, 0);
+            __syncthreads();
+            T *tmp = src;
+            src = dst;
+            dst = tmp;
+            continue;
+        }
         for (int item = threadIdx.x; item < cw * strips; item += blockDim.x) {
             const int x = lo + item % cw;
             const int y0 = lo + (item / cw) * V;
@@ -167,8 +189,9 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) batch_sweeps(const GridDev *__restrict__ grids, const Item *__restrict__ items,
-                                                         int nitems, const T *__restrict__ wtab, int *done, Ctl *ctl)
+__global__ void __launch_bounds__(kThreads)
+    batch_sweeps(const GridDev *__restrict__ grids, const Item *__restrict__ items, int nitems,
+                 const T *__restrict__ wtab, int *done, Ctl *ctl, unsigned long long wait_cycles, int block_sweep)
 {
     constexpr int V = sizeof(T) == 8 ? 4 : 8;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -184,10 +207,10 @@ __global__ void __launch_bounds__(kThreads) batch_sweeps(const GridDev *__restri
         const Item it = items[idx];
         const GridDev G = grids[it.g];
         if (it.s > 0 && threadIdx.x == 0) {
-            const int *dep = done + G.doff + it.s - 1;
+            const int *dep = it.s == block_sweep ? &ctl->never : done + G.doff + it.s - 1;
             const unsigned long long t0 = clock64();
             while (ld_acquire(dep) < G.ntiles) {
-                if (clock64() - t0 > kWaitCycles || *(volatile int *)&ctl->abort) {
+                if (clock64() - t0 > wait_cycles || *(volatile int *)&ctl->abort) {
                     atomicExch(&ctl->abort, 1);
                     s_go = 0;
                     break;
@@ -244,6 +267,8 @@ struct stencil_batch {
     size_t ws_bytes = 0;
     size_t ctl_off = 0;  // control word of the last run
     bool ran = false;
+    unsigned long long wait_cycles = gbs::bt::kWaitCycles;  // bounded dependency wait
+    int block_sweep = -1;  // test hook: sweep whose items wait on a counter nothing increments
     gbs::BatchCache cache;
 };
 
@@ -331,11 +356,13 @@ stencil_status launch_batch(stencil_batch *b, const Layout &L, cudaStream_t st, 
     bt::Ctl *ctl = (bt::Ctl *)(ws + L.ctl_off);
     if (b->dtype == STENCIL_F64)
         bt::batch_sweeps<double><<<grid, bt::kThreads, smem, st>>>(gd, items, L.nitems, (const double *)(ws + L.w_off),
-                                                                   done, ctl);
+                                                                   done, ctl, b->wait_cycles, b->block_sweep);
     else
         bt::batch_sweeps<float><<<grid, bt::kThreads, smem, st>>>(gd, items, L.nitems, (const float *)(ws + L.w_off),
-                                                                  done, ctl);
-    note_launch();
+                                                                  done, ctl, b->wait_cycles, b->block_sweep);
+    if (count) note_launch();
+    b->ctl_off = L.ctl_off;
+    b->ran = true;
     e = cudaGetLastError();
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "batch_sweeps launch");
 }
@@ -567,6 +594,26 @@ stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t strea
     e = cudaMemcpy(&ctl, (char *)batch->ws + batch->ctl_off, sizeof(ctl), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_status: reading the control word");
     if (ctl.abort) return fail(STENCIL_ERR_TIMEOUT, "stencil_batch: a dependency wait ran out; outputs incomplete");
+    return STENCIL_OK;
+}
+
+stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, const char *value)
+{
+    if (!batch || !key || !value) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_option: null argument");
+    char *end = nullptr;
+    const long long v = std::strtoll(value, &end, 10);
+    if (!*value || *end) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_option: value must be an integer");
+    const std::string k(key);
+    if (k == "wait_cycles") {
+        if (v < 1) return fail(STENCIL_ERR_INVALID_ARG, "wait_cycles must be >= 1");
+        batch->wait_cycles = (unsigned long long)v;
+    } else if (k == "debug_block_sweep") {
+        if (v < -1 || v == 0) return fail(STENCIL_ERR_INVALID_ARG, "debug_block_sweep must be -1 or >= 1");
+        batch->block_sweep = (int)v;
+    } else {
+        return fail(STENCIL_ERR_INVALID_ARG, "unknown batch option '" + k + "'");
+    }
+    drop_graph(batch->cache);
     return STENCIL_OK;
 }
 

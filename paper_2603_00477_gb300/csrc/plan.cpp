@@ -226,7 +226,7 @@ stencil_status dispatch(Plan *p)
                 } else {
                     c.tile[0] = 1;
                     c.tile[1] = p->dtype == STENCIL_F64 ? 64 : 128;
-                    c.tile[2] = p->dtype == STENCIL_F64 ? 64 : (prec == STENCIL_PREC_TF32X3 ? 64 : 128);
+                    c.tile[2] = p->dtype == STENCIL_F64 ? 64 : (prec == STENCIL_PREC_TF32 ? 64 : (prec == STENCIL_PREC_TF32X3 ? 32 : 64));
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec), P_cu,
                                             tc_peak(*p, prec, path), B);
@@ -405,6 +405,9 @@ stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, cons
                 return fail(STENCIL_ERR_INVALID_ARG, "tile: TX must be a multiple of 4, sides <= 1024");
         }
         for (int i = 0; i < 3; i++) trial.req_tile[i] = tl[i];
+    } else if (k == "debug_unmet_wait") {
+        if (v != "0" && v != "1") return fail(STENCIL_ERR_INVALID_ARG, "debug_unmet_wait must be 0 or 1");
+        trial.debug_unmet_wait = v == "1";
     } else {
         return fail(STENCIL_ERR_INVALID_ARG, "unknown option key '" + k + "'");
     }

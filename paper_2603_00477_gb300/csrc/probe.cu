@@ -10,19 +10,19 @@ namespace {
 __device__ unsigned long long g_probe_sink;
 
 template <typename T>
-__global__ void __launch_bounds__(256) fma_chains(int iters, T seed)
+__global__ void __launch_bounds__(256, 8) fma_chains(int iters, T seed)
 {
-    T a[8];
+    T a[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) a[j] = seed + (T)(threadIdx.x + j);
+    for (int j = 0; j < 16; ++j) a[j] = seed + (T)(threadIdx.x + j);
     const T m = (T)0.999999, c = (T)1e-7;
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+        for (int j = 0; j < 16; ++j) a[j] = fma(a[j], m, c);
     }
     T s = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) s += a[j];
+    for (int j = 0; j < 16; ++j) s += a[j];
     if (s == (T)-12345.0) g_probe_sink = 1;  // never true; keeps the chains alive
 }
 
@@ -44,7 +44,7 @@ stencil_status time_chains(int blocks, int iters, cudaStream_t st, double *flops
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(err, "probe timing");
-    *flops_per_s = (double)blocks * 256.0 * iters * 8.0 * 2.0 / (ms * 1e-3);
+    *flops_per_s = (double)blocks * 256.0 * iters * 16.0 * 2.0 / (ms * 1e-3);
     return STENCIL_OK;
 }
 
@@ -62,8 +62,8 @@ extern "C" stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_s
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_probe_peaks: device query");
     cudaStream_t st = (cudaStream_t)stream;
-    const int blocks = sms * 4;
-    stencil_status s = time_chains<double>(blocks, 1 << 8, st, &measured->cu_f64_flops);
+    const int blocks = sms * 8;  // 64 warps per SM, 16 independent chains each
+    stencil_status s = time_chains<double>(blocks, 1 << 7, st, &measured->cu_f64_flops);
     if (s != STENCIL_OK) return s;
-    return time_chains<float>(blocks, 1 << 14, st, &measured->cu_f32_flops);
+    return time_chains<float>(blocks, 1 << 13, st, &measured->cu_f32_flops);
 }
