@@ -235,6 +235,24 @@ stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_t
 stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in, void *out, int64_t steps,
                                    stencil_stream_t stream);
 
+/* One autotuning measurement. */
+typedef struct {
+    int path, precision, t;
+    double model_gstencils;     /* the dispatcher's (model) prediction */
+    double measured_gstencils;  /* point-updates/s / 1e9 on the caller's buffers */
+} stencil_tune_result;
+
+/* Autotuner seeded by the model: runs every (path, precision, t) the plan's
+ * options allow, in the model's order, `reps` times `steps` steps on the
+ * caller's device buffers (after one warm-up run each), times them with CUDA
+ * events on `stream`, and makes the fastest the plan's choice.  Uses the
+ * plan's workspace like stencil_run; `out` is overwritten.  Writes up to
+ * max_results rows to `results` (may be null) and the number of candidates
+ * run to *n_results (may be null).  Synchronises `stream`. */
+stencil_status stencil_plan_autotune(stencil_plan *plan, const void *in, void *out, int64_t steps, int reps,
+                                     stencil_stream_t stream, stencil_tune_result *results, int max_results,
+                                     int *n_results);
+
 /* Release a plan (never frees caller workspace).  Null is ignored. */
 void stencil_plan_destroy(stencil_plan *plan);
 

@@ -57,6 +57,11 @@ class stencil_grid_desc(ctypes.Structure):
                 ("weights", ctypes.POINTER(ctypes.c_double))]
 
 
+class stencil_tune_result(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("t", ctypes.c_int),
+                ("model_gstencils", ctypes.c_double), ("measured_gstencils", ctypes.c_double)]
+
+
 class stencil_model_in(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("d", ctypes.c_int), ("r", ctypes.c_int), ("t", ctypes.c_int),
                 ("dtype_bytes", ctypes.c_int), ("sparsity", ctypes.c_double), ("beta", ctypes.c_double),
@@ -104,6 +109,9 @@ def load() -> ctypes.CDLL:
     L.stencil_run_noalloc.restype = st
     L.stencil_run_host.argtypes = [vp, vp, vp, i64, vp]
     L.stencil_run_host.restype = st
+    L.stencil_plan_autotune.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.POINTER(stencil_tune_result),
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.stencil_plan_autotune.restype = st
     L.stencil_plan_destroy.argtypes = [vp]
     L.stencil_plan_destroy.restype = None
     L.stencil_model_predict.argtypes = [ctypes.POINTER(stencil_model_in), ctypes.POINTER(stencil_model_out)]
@@ -246,6 +254,17 @@ def stencil_device_status(stream=None) -> None:
     _check(load().stencil_device_status(_stream_handle(stream)), "stencil_device_status")
 
 
+def stencil_plan_autotune(plan: int, in_ptr: int, out_ptr: int, steps: int, reps: int = 2, stream=None,
+                          max_results: int = 64) -> list:
+    res = (stencil_tune_result * max_results)()
+    n = ctypes.c_int(0)
+    _check(load().stencil_plan_autotune(plan, in_ptr, out_ptr, int(steps), int(reps), _stream_handle(stream), res,
+                                        max_results, ctypes.byref(n)), "stencil_plan_autotune")
+    return [{"path": PATH_NAMES[r.path], "precision": PREC_NAMES[r.precision], "t": r.t,
+             "model_gstencils": r.model_gstencils, "measured_gstencils": r.measured_gstencils}
+            for r in res[:min(n.value, max_results)]]
+
+
 def stencil_plan_destroy(plan: int) -> None:
     if plan:
         load().stencil_plan_destroy(plan)
@@ -344,6 +363,12 @@ class Plan:
         self._check_tensor(x_out, "out")
         self.ensure_workspace(x_in.device)
         stencil_run(self.handle, x_in.data_ptr(), x_out.data_ptr(), steps, stream)
+
+    def autotune(self, x_in, x_out, steps: int, reps: int = 2, stream=None) -> list:
+        self._check_tensor(x_in, "in")
+        self._check_tensor(x_out, "out")
+        self.ensure_workspace(x_in.device)
+        return stencil_plan_autotune(self.handle, x_in.data_ptr(), x_out.data_ptr(), steps, reps, stream)
 
     def run_host(self, h_in, h_out, steps: int, device="cuda", stream=None):
         """h_in/h_out: CPU tensors (pinned for full speed) of the stored shape."""

@@ -280,203 +280,254 @@ __global__ void __launch_bounds__(128) tc2d_sweep(const float *__restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined TF32 / TF32x3 sweep (persistent CTAs).  Per CTA and tile:
-//   1. the raw FP32 input tile lands by cp.async directly in the chunk-column
-//      layout of the A operand (double-buffered across tiles, issued as soon
-//      as the MMAs of the previous tile have released the buffer);
-//   2. an in-place pass rounds it to TF32 (round to nearest) and, for
-//      TF32x3, writes the lo part;
-//   3. one thread issues the tile's MMAs into one of two TMEM accumulator
-//      sets and commits them to that set's mbarrier;
-//   4. meanwhile the CTA reads the previous tile's accumulators back and
-//      stores them (float4 when aligned).
-// Output tiles are aligned to stored column 0 (X0 = bx * TX) so that rows
-// whose stored pitch is a multiple of four floats store with 16-byte writes.
+// Warp-specialised TF32 / TF32x3 sweep (persistent CTAs, 160 threads).
+//
+// An MMA of M=128 rows costs a fixed ~47 cycles for any N <= 64 (measured
+// on GB300 for kind::tf32, K=8), so each MMA covers TN = 16 or 32 output
+// columns (the Toeplitz block is TN x 8) rather than 8: four times the work
+// per instruction for a lower sparsity factor S.  Warp 4 only issues MMAs;
+// warps 0-3 load (cp.async straight into the chunk-column A layout,
+// double-buffered), round / split, and drain the accumulators of the
+// previous tile (tcgen05.ld, double-buffered TMEM).  Three mbarriers per
+// buffer pair hand work over: full[b] (operands of buffer b ready, 128
+// arrivals), done[b] (the MMAs reading buffer b and writing accumulator set
+// b completed, tcgen05.commit), free[b] (accumulator set b read, 128
+// arrivals).  Every wait is bounded; a wait that runs out sets the abort flag
+// and every warp leaves its loop.
 // ---------------------------------------------------------------------------
-template <int PREC, int NACC>
-__global__ void __launch_bounds__(128, 1)
-    tc2d_pipe(const float *__restrict__ in, float *__restrict__ out, const __grid_constant__ TcParams p,
-              int ntiles, int ntx)
+template <int PREC, int TN_, int NACC>
+__global__ void __launch_bounds__(288, 1)
+    tc2d_ws(const float *__restrict__ in, float *__restrict__ out, const __grid_constant__ TcParams p, int ntiles,
+            int ntx)
 {
     constexpr bool SPLIT = PREC == P_TF32X3;
-    constexpr int E = 4, TX = NACC * TN;
-    constexpr uint32_t kSet = NACC * TN * (SPLIT ? 2 : 1);  // TMEM columns per accumulator set
+    constexpr int E = 4, TX = NACC * TN_;
+    constexpr uint32_t kSet = NACC * TN_ * (SPLIT ? 2 : 1);
     constexpr uint32_t kCols = 2 * kSet;
-    constexpr uint32_t kCorr = NACC * TN;
-    static_assert(kCols >= 32 && (kCols & (kCols - 1)) == 0, "TMEM columns: power of two >= 32");
+    constexpr uint32_t kCorr = NACC * TN_;
+    constexpr uint32_t kBlk = (TN_ / 8) * 256;  // bytes of one Toeplitz block (TN rows x 8 k)
+    static_assert(kCols >= 32 && kCols <= 512 && (kCols & (kCols - 1)) == 0, "TMEM columns");
 
     extern __shared__ __align__(1024) unsigned char smem[];
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 8);  // two barriers: 8, 16
+    int *abort_flag = reinterpret_cast<int *>(smem + 4);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 16);   // [2]
+    uint64_t *done = reinterpret_cast<uint64_t *>(smem + 32);   // [2]
+    uint64_t *freeb = reinterpret_cast<uint64_t *>(smem + 48);  // [2]
     const int R = p.R, HS = p.hs, NCH = p.nch, nkb = p.nkb;
     const int lines = 2 * R + 1;
     const uint32_t a_bytes = (uint32_t)NCH * HS * 16;
-    const uint32_t b_bytes = (uint32_t)lines * nkb * 256;
+    const uint32_t b_bytes = (uint32_t)lines * nkb * kBlk;
     unsigned char *B0 = smem + 128;
     unsigned char *B1 = B0 + (SPLIT ? b_bytes : 0);
     unsigned char *abase = B0 + b_bytes * (SPLIT ? 2 : 1);
     float *Ahi[2] = {reinterpret_cast<float *>(abase), reinterpret_cast<float *>(abase + a_bytes)};
-    float *Alo = reinterpret_cast<float *>(abase + 2 * a_bytes);
+    float *Alo[2] = {reinterpret_cast<float *>(abase + 2 * a_bytes), reinterpret_cast<float *>(abase + 3 * a_bytes)};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t Ey = p.Ey, Ex = p.Ex, rh = p.rh;
     const int64_t ny = Ey - 2 * rh, nx = Ex - 2 * rh;
 
     if (warp == 0) tmem_alloc(tmem_slot, kCols);
     if (tid == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        *abort_flag = 0;
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 256);   // all eight worker warps
+            mbar_init(&done[b], 1);
+            mbar_init(&freeb[b], 128);  // the four epilogue warps
+        }
         fence_mbar_init();
     }
-    const int bent = lines * nkb * 64;
+    // Toeplitz blocks: block (line, kb) = TN rows (n) x 8 k, K-major core
+    // matrices (n-group i, k-chunk j) at i*256 + j*128
+    const int bent = lines * nkb * TN_ * 8;
     for (int idx = tid; idx < bent; idx += blockDim.x) {
-        const int k = idx % 8, n = (idx / 8) % 8, blk = idx / 64;
+        const int k = idx % 8, n = (idx / 8) % TN_, blk = idx / (8 * TN_);
         const int ai = blk / nkb, kb = blk % nkb;
         const int b = kb * 8 + k - n - R;
         const double wv = (b >= -R && b <= R) ? p.w[ai * lines + (b + R)] : 0.0;
-        const uint32_t off = blk * 256 + (k / E) * 128 + n * 16 + (k % E) * 4;
+        const uint32_t off = blk * kBlk + (n / 8) * 256 + (k / E) * 128 + (n % 8) * 16 + (k % E) * 4;
         split_store_w<SPLIT ? P_TF32X3 : P_TF32>(B0 + off, B1 + off, wv);
     }
-
-    const int rows = TM + 2 * R, cols = NCH * E;
-    auto origin = [&](int id, int64_t *Y0, int64_t *X0) {
-        *Y0 = rh + (int64_t)(id / ntx) * TM;
-        *X0 = (int64_t)(id % ntx) * TX;
-    };
-    auto prefetch = [&](int id, float *dst) {
-        int64_t Y0, X0;
-        origin(id, &Y0, &X0);
-        for (int row = warp; row < rows; row += 4) {
-            const int64_t gy = Y0 - R + row;
-            const bool rowok = gy >= 0 && gy < Ey;
-            for (int x = lane; x < cols; x += 32) {
-                const int64_t gx = X0 - R + x;
-                const bool ok = rowok && gx >= 0 && gx < Ex;
-                cu::cp_async_elem<4>(reinterpret_cast<unsigned char *>(dst) + (x / E) * HS * 16 + row * 16 + (x % E) * 4,
-                                     ok ? in + gy * Ex + gx : in, ok);
-            }
-        }
-    };
-    auto epilogue = [&](int id, uint32_t set_base) {
-        int64_t Y0, X0;
-        origin(id, &Y0, &X0);
-        const int m = warp * 32 + lane;
-        const int64_t gy = Y0 + m, iy = gy - rh;
-        const bool rowok = iy < ny && iy >= p.band && ny - 1 - iy >= p.band;
-        const uint32_t lane_base = set_base + ((uint32_t)(warp * 32) << 16);
-        for (int q = 0; q < NACC; ++q) {
-            uint32_t v[8], c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            tmem_ld_32x32b_x8(lane_base + q * TN, v);
-            if (SPLIT) tmem_ld_32x32b_x8(lane_base + kCorr + q * TN, c);
-            tmem_ld_wait();
-            if (!rowok) continue;
-            float f[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) f[j] = __uint_as_float(v[j]) + (SPLIT ? __uint_as_float(c[j]) : 0.0f);
-            const int64_t gx0 = X0 + q * TN;
-            float *dst = out + gy * Ex + gx0;
-            const bool full = gx0 >= rh + p.band && gx0 + 7 < Ex - rh - p.band;
-            if (full && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-                reinterpret_cast<float4 *>(dst)[0] = make_float4(f[0], f[1], f[2], f[3]);
-                reinterpret_cast<float4 *>(dst)[1] = make_float4(f[4], f[5], f[6], f[7]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int64_t ix = gx0 + j - rh;
-                    if (ix >= p.band && ix < nx - p.band) dst[j] = f[j];
-                }
-            }
-        }
-    };
-
+    fence_proxy_async_smem();
     fence_before_thread_sync();
     __syncthreads();
     fence_after_thread_sync();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = instr_desc(kFmtTF32, TM, TN);
-    const uint32_t lbo_a = (uint32_t)HS * 16;
-    uint32_t phase[2] = {0, 0};
-    bool pending[2] = {false, false};  // a commit on this barrier not yet waited for
-    bool bad = false;
-    int my = 0, prev = -1;
 
-    if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, Ahi[0]);
-    cu::cp_async_commit();
-    for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++my) {
-        const int cur = my & 1;
-        cu::cp_async_wait_group<0>();
-        __syncthreads();
-        if (my > 0) {  // MMAs of the previous tile done: its A buffer, Alo and accumulators are free
-            const int pb = cur ^ 1;
-            if (!wait_mbar_cycles(&mbar[pb], phase[pb])) {
-                bad = true;
-                break;
+    auto bounded_wait = [&](uint64_t *bar, uint32_t parity, unsigned long long limit) -> bool {
+        const unsigned long long t0 = clock64();
+        while (!mbar_try_wait(bar, parity)) {
+            if (*(volatile int *)abort_flag) return false;
+            if (clock64() - t0 > limit) {
+                atomicExch(abort_flag, 1);
+                return false;
             }
-            phase[pb] ^= 1;
-            pending[pb] = false;
-            fence_after_thread_sync();
         }
-        const int nid = id + gridDim.x;
-        if (nid < ntiles) prefetch(nid, Ahi[cur ^ 1]);
-        cu::cp_async_commit();
-        // round to TF32 in place; split forms also write the lo part
-        const int words = (int)(a_bytes / 4);
-        float *A = Ahi[cur];
-        for (int i = tid; i < words; i += blockDim.x) {
-            const float u = A[i];
-            const float h = to_tf32(u);
-            A[i] = h;
-            if (SPLIT) Alo[i] = to_tf32(u - h);
-        }
-        fence_proxy_async_smem();
-        fence_before_thread_sync();
-        __syncthreads();
-        fence_after_thread_sync();
-        if (tid == 0) {
-            const uint32_t a0 = smem_u32(A), a1 = smem_u32(Alo), b0 = smem_u32(B0), b1 = smem_u32(B1);
-            const uint32_t dset = tmem + cur * kSet;
-            for (int q = 0; q < NACC; ++q) {
-                uint32_t acc = 0;
-                const uint32_t d = dset + q * TN, dc = d + kCorr;
-                for (int ai = 0; ai < lines; ++ai) {
-                    for (int kb = p.kb_lo[ai]; kb <= p.kb_hi[ai]; ++kb) {
-                        const uint32_t aoff = (uint32_t)(q * 2 + 2 * kb) * lbo_a + ai * 16;
-                        const uint32_t boff = (uint32_t)(ai * nkb + kb) * 256;
-                        const uint64_t da0 = smem_desc(a0 + aoff, lbo_a, 128);
-                        const uint64_t db0 = smem_desc(b0 + boff, 128, 256);
-                        mma_tf32(d, da0, db0, idesc, acc);
-                        if (SPLIT) {
-                            mma_tf32(dc, da0, smem_desc(b1 + boff, 128, 256), idesc, acc);
-                            mma_tf32(dc, smem_desc(a1 + aoff, lbo_a, 128), db0, idesc, 1);
+        return true;
+    };
+    auto origin = [&](int id, int64_t *Y0, int64_t *X0) {
+        *Y0 = rh + (int64_t)(id / ntx) * TM;
+        *X0 = (int64_t)(id % ntx) * TX;
+    };
+
+    if (warp == 8) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(kFmtTF32, TM, TN_);
+            const uint32_t lbo_a = (uint32_t)HS * 16;
+            const uint32_t b0 = smem_u32(B0), b1 = smem_u32(B1);
+            int k = 0;
+            for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++k) {
+                const int b = k & 1;
+                if (!bounded_wait(&full[b], (k >> 1) & 1, kWaitCycles)) break;
+                if (k >= 2 && !bounded_wait(&freeb[b], ((k - 2) >> 1) & 1, kWaitCycles)) break;
+                fence_after_thread_sync();
+                // Descriptors advance by adding offsets in 16-byte units to the
+                // start-address field (bits 0-13; every address < 256 KB).
+                const uint64_t da_base = smem_desc(smem_u32(Ahi[b]), lbo_a, 128);
+                const uint64_t db_base = smem_desc(b0, 128, 256);
+                const uint64_t dlo_a = (uint64_t)((smem_u32(Alo[b]) - smem_u32(Ahi[b])) >> 4);
+                const uint64_t dlo_b = (uint64_t)((b1 - b0) >> 4);
+                const uint64_t kb_step_a = (uint64_t)2 * HS;   // two chunk columns
+                const uint64_t blk16 = kBlk >> 4;
+                const uint32_t dset = tmem + b * kSet;
+                for (int q = 0; q < NACC; ++q) {
+                    uint32_t acc = 0;
+                    const uint32_t d = dset + q * TN_, dc = d + kCorr;
+                    const uint64_t da_q = da_base + (uint64_t)(q * (TN_ / E)) * HS;
+                    for (int ai = 0; ai < lines; ++ai) {
+                        const int klo = p.kb_lo[ai], khi = p.kb_hi[ai];
+                        uint64_t da = da_q + (uint64_t)ai + (uint64_t)klo * kb_step_a;
+                        uint64_t db = db_base + (uint64_t)(ai * nkb + klo) * blk16;
+                        for (int kb = klo; kb <= khi; ++kb) {
+                            mma_tf32(d, da, db, idesc, acc);
+                            if (SPLIT) {
+                                mma_tf32(dc, da, db + dlo_b, idesc, acc);
+                                mma_tf32(dc, da + dlo_a, db, idesc, 1);
+                            }
+                            acc = 1;
+                            da += kb_step_a;
+                            db += blk16;
                         }
-                        acc = 1;
+                    }
+                }
+                mma_commit(&done[b]);
+            }
+            // let the last MMAs finish before TMEM can be freed (no early exit
+            // on abort here: this wait protects the TMEM the MMAs write)
+            if (k >= 1) wait_mbar_cycles(&done[(k - 1) & 1], ((k - 1) >> 1) & 1);
+            if (k >= 2) wait_mbar_cycles(&done[(k - 2) & 1], ((k - 2) >> 1) & 1);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- loaders / converters (warps 0-7), epilogue (warps 0-3) -----
+        const int rows = TM + 2 * R, cols = NCH * E;
+        auto prefetch = [&](int id, float *dst) {
+            int64_t Y0, X0;
+            origin(id, &Y0, &X0);
+            for (int row = warp; row < rows; row += 8) {
+                const int64_t gy = Y0 - R + row;
+                const bool rowok = gy >= 0 && gy < Ey;
+                for (int x = lane; x < cols; x += 32) {
+                    const int64_t gx = X0 - R + x;
+                    const bool ok = rowok && gx >= 0 && gx < Ex;
+                    cu::cp_async_elem<4>(reinterpret_cast<unsigned char *>(dst) + (x / E) * HS * 16 + row * 16 +
+                                             (x % E) * 4,
+                                         ok ? in + gy * Ex + gx : in, ok);
+                }
+            }
+        };
+        auto epilogue = [&](int id, uint32_t set_base) {
+            int64_t Y0, X0;
+            origin(id, &Y0, &X0);
+            const int m = warp * 32 + lane;
+            const int64_t gy = Y0 + m, iy = gy - rh;
+            const bool rowok = iy < ny && iy >= p.band && ny - 1 - iy >= p.band;
+            const uint32_t lane_base = set_base + ((uint32_t)(warp * 32) << 16);
+            for (int q = 0; q < NACC; ++q) {
+#pragma unroll
+                for (int h = 0; h < TN_ / 8; ++h) {
+                    uint32_t v[8], c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    tmem_ld_32x32b_x8(lane_base + q * TN_ + h * 8, v);
+                    if (SPLIT) tmem_ld_32x32b_x8(lane_base + kCorr + q * TN_ + h * 8, c);
+                    tmem_ld_wait();
+                    if (!rowok) continue;
+                    float f[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        f[j] = __uint_as_float(v[j]) + (SPLIT ? __uint_as_float(c[j]) : 0.0f);
+                    const int64_t gx0 = X0 + q * TN_ + h * 8;
+                    float *dst = out + gy * Ex + gx0;
+                    const bool fullrow = gx0 >= rh + p.band && gx0 + 7 < Ex - rh - p.band;
+                    if (fullrow && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+                        reinterpret_cast<float4 *>(dst)[0] = make_float4(f[0], f[1], f[2], f[3]);
+                        reinterpret_cast<float4 *>(dst)[1] = make_float4(f[4], f[5], f[6], f[7]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int64_t ix = gx0 + j - rh;
+                            if (ix >= p.band && ix < nx - p.band) dst[j] = f[j];
+                        }
                     }
                 }
             }
-            mma_commit(&mbar[cur]);
+        };
+
+        int k = 0, prev = -1;
+        if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, Ahi[0]);
+        cu::cp_async_commit();
+        bool ok = true;
+        for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++k) {
+            const int b = k & 1;
+            cu::cp_async_wait_group<0>();
+            named_bar_sync(1, 256);
+            if (*(volatile int *)abort_flag) {
+                ok = false;
+                break;
+            }
+            // round to TF32 in place (and split off the lo part)
+            const int words = (int)(a_bytes / 4);
+            float *A = Ahi[b], *L = Alo[b];
+            for (int i = tid; i < words; i += 256) {
+                const float u = A[i];
+                const float hi = to_tf32(u);
+                A[i] = hi;
+                if (SPLIT) L[i] = to_tf32(u - hi);
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&full[b]);
+            if (k >= 1) {  // tile k-1: its MMAs released buffer b^1 and filled accumulator set b^1
+                if (!bounded_wait(&done[b ^ 1], ((k - 1) >> 1) & 1, kWaitCycles)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_thread_sync();
+            }
+            // the next tile's loads go out first; the epilogue hides their latency
+            const int nid = id + gridDim.x;
+            if (nid < ntiles) prefetch(nid, Ahi[b ^ 1]);
+            cu::cp_async_commit();
+            if (k >= 1 && warp < 4) {
+                epilogue(prev, tmem + (b ^ 1) * kSet);
+                fence_before_thread_sync();
+                mbar_arrive(&freeb[b ^ 1]);
+            }
+            prev = id;
         }
-        pending[cur] = true;
-        __syncwarp();
-        if (prev >= 0) epilogue(prev, tmem + (cur ^ 1) * kSet);
-        prev = id;
+        if (ok && prev >= 0) {
+            const int lb = (k - 1) & 1;
+            ok = bounded_wait(&done[lb], ((k - 1) >> 1) & 1, kWaitCycles);
+            fence_after_thread_sync();
+            // test hook: the barrier's next phase is never completed
+            if (ok && p.debug_unmet) ok = bounded_wait(&done[lb], (((k - 1) >> 1) & 1) ^ 1, kDebugWaitCycles);
+            if (ok && warp < 4) epilogue(prev, tmem + lb * kSet);
+        }
+        cu::cp_async_wait_group<0>();
+        if (!ok) atomicExch(abort_flag, 1);
     }
-    if (!bad && prev >= 0) {
-        const int lb = (my - 1) & 1;
-        bool ok = wait_mbar_cycles(&mbar[lb], phase[lb]);
-        if (ok) pending[lb] = false;
-        fence_after_thread_sync();
-        // test hook: the barrier now sits in a phase no arrival completes
-        if (ok && p.debug_unmet) ok = wait_mbar_cycles(&mbar[lb], phase[lb] ^ 1, kDebugWaitCycles);
-        if (ok) epilogue(prev, tmem + lb * kSet);
-        else bad = true;
-    }
-    if (bad) {
-        atomicExch(&g_tc_error, 1);
-        for (int b = 0; b < 2; ++b)  // let MMAs in flight finish before TMEM is freed
-            if (pending[b]) wait_mbar_cycles(&mbar[b], phase[b]);
-    }
-    cu::cp_async_wait_group<0>();
     fence_before_thread_sync();
     __syncthreads();
+    if (tid == 0 && *(volatile int *)abort_flag) atomicExch(&g_tc_error, 1);
     if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
@@ -617,48 +668,55 @@ stencil_status launch_tc2d(const Plan &p, const void *in, void *out, int t, cuda
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_sweep launch");
 }
 
-template <int PREC, int NACC>
-stencil_status launch_tc2d_pipe(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+template <int PREC, int TN_, int NACC>
+stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t, cudaStream_t st, bool *fits)
 {
     using namespace tcs;
-    constexpr int TX = NACC * TN;
+    constexpr int TX = NACC * TN_;
     static int cached = 0;
-    static int occ_smem = -1, occ_blocks = 0;
     TcParams tp;
     TcLines L;
-    stencil_status s = fill_params(p, t, TN, 8, &tp, &L);
+    stencil_status s = fill_params(p, t, TN_, 8, &tp, &L);
     if (s != STENCIL_OK) return s;
     const int R = tp.R;
     tp.hs = TM + 2 * R;
     if (tp.hs % 2 == 0) tp.hs += 1;
-    tp.nch = (TN * (NACC - 1) + L.kext) / 4;
+    tp.nch = (TN_ * (NACC - 1) + L.kext) / 4;
     const bool split = PREC == P_TF32X3;
     const size_t a_bytes = (size_t)tp.nch * tp.hs * 16;
-    const size_t b_bytes = (size_t)(2 * R + 1) * L.nkb * 256;
-    const size_t smem = 128 + b_bytes * (split ? 2 : 1) + a_bytes * (split ? 3 : 2);
-    if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core tile does not fit in shared memory");
-    auto kern = tc2d_pipe<PREC, NACC>;
+    const size_t b_bytes = (size_t)(2 * R + 1) * L.nkb * (TN_ / 8) * 256;
+    const size_t smem = 128 + b_bytes * (split ? 2 : 1) + a_bytes * (split ? 4 : 2);
+    *fits = smem <= 227 * 1024;
+    if (!*fits) return STENCIL_OK;
+    auto kern = tc2d_ws<PREC, TN_, NACC>;
     s = ensure_smem((const void *)kern, smem, &cached);
     if (s != STENCIL_OK) return s;
-    if (occ_smem != (int)smem) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, 128, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        occ_smem = (int)smem;
-    }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // TMEM: each resident CTA holds 2 * NACC * 8 (x2 split) columns of 512
-    const int tmem_cols = 2 * NACC * TN * (split ? 2 : 1);
-    const int per_sm = std::max(1, std::min(occ_blocks, 512 / tmem_cols));
     const int64_t nty = (p.dims[1] + TM - 1) / TM, ntx = (p.ext[2] + TX - 1) / TX;
     const int64_t ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)per_sm * sms);
-    kern<<<grid, 128, smem, st>>>((const float *)in, (float *)out, tp, (int)ntiles, (int)ntx);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
+    kern<<<grid, 288, smem, st>>>((const float *)in, (float *)out, tp, (int)ntiles, (int)ntx);
     note_launch();
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_pipe launch");
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_ws launch");
+}
+
+// Widest MMA N whose operands fit in shared memory (the rule the dispatcher
+// uses to report S, tc_ws_ntile).
+template <int PREC>
+stencil_status launch_tc2d_ws(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+{
+    bool fits = false;
+    const int tn = tc_ws_ntile(p.pat.shape, p.pat.r, t, PREC == tcs::P_TF32X3);
+    stencil_status s;
+    if (tn == 32) s = launch_tc2d_ws_n<PREC, 32, 2>(p, in, out, t, st, &fits);
+    else if (tn == 16) s = launch_tc2d_ws_n<PREC, 16, 2>(p, in, out, t, st, &fits);
+    else s = launch_tc2d_ws_n<PREC, 8, 4>(p, in, out, t, st, &fits);
+    if (s != STENCIL_OK) return s;
+    return fits ? STENCIL_OK : fail(STENCIL_ERR_UNSUPPORTED, "tensor-core tile does not fit in shared memory");
 }
 
 stencil_status launch_dmma2d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
@@ -696,8 +754,8 @@ stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, 
         s = launch_dmma2d(p, in, out, t, st);
     } else {
         switch (p.precision) {
-        case STENCIL_PREC_TF32: s = launch_tc2d_pipe<tcs::P_TF32, 8>(p, in, out, t, st); break;
-        case STENCIL_PREC_TF32X3: s = launch_tc2d_pipe<tcs::P_TF32X3, 4>(p, in, out, t, st); break;
+        case STENCIL_PREC_TF32: s = launch_tc2d_ws<tcs::P_TF32>(p, in, out, t, st); break;
+        case STENCIL_PREC_TF32X3: s = launch_tc2d_ws<tcs::P_TF32X3>(p, in, out, t, st); break;
         case STENCIL_PREC_BF16X3: s = launch_tc2d<tcs::P_BF16X3, 8>(p, in, out, t, st); break;
         default: return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: precision");
         }

@@ -119,6 +119,8 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     if (dtype == STENCIL_F64) g.k_inst = 4;                    // FP64 MMA m8n8k4
     else if (precision == STENCIL_PREC_BF16X3) g.k_inst = 16;  // kind::f16 K = 16
     else g.k_inst = 8;                                         // kind::tf32 K = 8
+    if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
+        g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
     (void)path;
     if (d == 2) {
         TcLines L = tc_lines_2d(shape, r, t, g.n_tile, g.k_inst);
@@ -167,7 +169,31 @@ static double beta_of(int precision)
     return (precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3) ? 3.0 : 1.0;
 }
 
-stencil_status dispatch(Plan *p)
+struct Cand {
+    int path, prec, t;
+    double gst;
+    int tile[3];
+};
+
+static stencil_status enumerate(Plan *p, std::vector<Cand> *out);
+
+stencil_status dispatch_candidates(Plan *p, std::vector<int> *paths, std::vector<int> *precs, std::vector<int> *ts,
+                                   std::vector<double> *model)
+{
+    std::vector<Cand> c;
+    stencil_status s = enumerate(p, &c);
+    if (s != STENCIL_OK) return s;
+    std::stable_sort(c.begin(), c.end(), [](const Cand &a, const Cand &b) { return a.gst > b.gst; });
+    for (auto &x : c) {
+        paths->push_back(x.path);
+        precs->push_back(x.prec);
+        ts->push_back(x.t);
+        model->push_back(x.gst);
+    }
+    return STENCIL_OK;
+}
+
+static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
 {
     const stencil_peaks &pk = peaks();
     const int D = (int)p->elem_bytes();
@@ -193,12 +219,8 @@ stencil_status dispatch(Plan *p)
         paths = {p->req_path};
     }
 
-    struct Cand {
-        int path, prec, t;
-        double gst;
-        int tile[3];
-    };
-    std::vector<Cand> cands;
+    std::vector<Cand> &cands = *out;
+    cands.clear();
     for (int path : paths) {
         for (int prec : precs) {
             if (path == STENCIL_PATH_CUDA_CORE) {
@@ -238,6 +260,19 @@ stencil_status dispatch(Plan *p)
     }
     if (cands.empty())
         return fail(STENCIL_ERR_UNSUPPORTED, "no kernel for this (path, precision, shape, d, r, dtype)");
+    return STENCIL_OK;
+}
+
+stencil_status dispatch(Plan *p)
+{
+    const stencil_peaks &pk = peaks();
+    const int D = (int)p->elem_bytes();
+    const int shape = p->pat.shape, d = p->pat.d, r = p->pat.r;
+    const double P_cu = p->dtype == STENCIL_F64 ? pk.cu_f64_flops : pk.cu_f32_flops;
+    const double B = pk.hbm_bytes_per_s;
+    std::vector<Cand> cands;
+    stencil_status es = enumerate(p, &cands);
+    if (es != STENCIL_OK) return es;
     double best = 0;
     for (auto &c : cands) best = std::max(best, c.gst);
     const Cand *pick = nullptr;

@@ -65,4 +65,24 @@ inline TcLines tc_lines_2d(int shape, int r, int t, int n_tile, int k_inst)
     return L;
 }
 
+// MMA N (output columns per Toeplitz block) of the warp-specialised TF32 /
+// TF32x3 kernel: the widest of 32, 16, 8 whose operands fit in 227 KB of
+// shared memory -- B blocks (x2 split) plus double-buffered A tiles (hi, and
+// lo when split) of 128 + 2R rows (odd) by (NACC-1)*N + kext columns.
+inline int tc_ws_ntile(int shape, int r, int t, bool split)
+{
+    const int R = t * r;
+    const int hs = (128 + 2 * R) | 1;
+    const int cand[3][2] = {{32, 2}, {16, 2}, {8, 4}};
+    for (auto &c : cand) {
+        const int n = c[0], nacc = c[1];
+        TcLines L = tc_lines_2d(shape, r, t, n, 8);
+        const long a = (long)((n * (nacc - 1) + L.kext) / 4) * hs * 16;
+        const long b = (long)(2 * R + 1) * L.nkb * (n / 8) * 256;
+        const long smem = 128 + b * (split ? 2 : 1) + a * (split ? 4 : 2);
+        if (smem <= 227 * 1024) return n;
+    }
+    return 8;
+}
+
 }  // namespace gbs

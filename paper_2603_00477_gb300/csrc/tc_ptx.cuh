@@ -144,6 +144,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t phase
     return false;
 }
 
+// Arrive (once per calling thread) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Barrier among a subset of the CTA's warps (named barrier `id`, `count`
+// threads, a multiple of 32).
+__device__ __forceinline__ void named_bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // ---- TMEM -> registers -----------------------------------------------------
 // Warp w of the CTA reads TMEM lanes 32(w%4) .. +31; thread i gets lane
 // 32(w%4)+i, columns col .. col+7 (32-bit each).

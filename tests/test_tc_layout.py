@@ -37,7 +37,7 @@ def test_toeplitz_times_im2col_equals_fused_sweep(shape, r, t, dtype, prec):
     lay, lo, hi, Bop = B.stencil_plan_tc_layout(p.handle, t)
     R, n, ki, nkb = lay["R"], lay["n_tile"], lay["k_inst"], lay["nkb"]
     assert R == t * r and lay["kext"] == nkb * ki and lay["kext"] >= n + 2 * R
-    dims = (30, 8 * 5)
+    dims = (30, 96)  # a multiple of every MMA N the layouts use (8, 16, 32)
     rng = np.random.default_rng(3)
     u = rng.uniform(0, 1, size=(dims[0] + 2 * R, dims[1] + 2 * R + lay["kext"]))
     # im2col: window of output columns x0..x0+n-1 of row y for line a is
@@ -65,11 +65,19 @@ def test_toeplitz_times_im2col_equals_fused_sweep(shape, r, t, dtype, prec):
     p.close()
 
 
-@pytest.mark.parametrize("t,S", [(1, 5 / 16), (2, 9 / 16), (3, 13 / 24), (4, 17 / 24)])
-def test_sparsity_tf32_box2d2r(t, S):
-    """Box lines are all 2R+1 wide: S = (2R+1) / roundup(8 + 2R, 8)."""
-    p, _ = _plan("box", 2, "f32", "tf32")
-    assert B.stencil_plan_tc_layout(p.handle, t, with_B=False)[0]["sparsity"] == pytest.approx(S)
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3"])
+@pytest.mark.parametrize("t", [1, 2, 3, 4])
+def test_sparsity_tf32_box2d2r(prec, t):
+    """Box lines are all 2R+1 wide: S = (2R+1) / roundup(N + 2R, 8) for the
+    MMA width N the kernel uses (32 when its operands fit, else 16 or 8)."""
+    p, _ = _plan("box", 2, "f32", prec)
+    lay = B.stencil_plan_tc_layout(p.handle, t, with_B=False)[0]
+    R = 2 * t
+    n = lay["n_tile"]
+    assert n in (8, 16, 32)
+    assert lay["sparsity"] == pytest.approx((2 * R + 1) / (-(-(n + 2 * R) // 8) * 8))
+    if prec == "tf32":
+        assert n == 32  # single-operand TF32 fits N = 32 up to R = 8
     p.close()
 
 
@@ -86,10 +94,11 @@ def test_plan_info_reports_layout_sparsity_and_alpha():
     p, _ = _plan("box", 2, "f32", "tf32", dims=(1000, 1000))
     p.set_option("t", 3)
     info = p.info()
+    S = B.stencil_plan_tc_layout(p.handle, 3, with_B=False)[0]["sparsity"]
     assert info["path"] == B.PATH_TENSOR_CORE and info["t"] == 3
-    assert info["sparsity"] == pytest.approx(13 / 24)
+    assert info["sparsity"] == pytest.approx(S) and S == pytest.approx(13 / 48)
     assert info["alpha"] == pytest.approx(model.alpha("box", 2, 2, 3))
-    assert info["intensity"] == pytest.approx(model.I_tc("box", 2, 2, 3, 4, 13 / 24))
+    assert info["intensity"] == pytest.approx(model.I_tc("box", 2, 2, 3, 4, S))
     p.close()
 
 
