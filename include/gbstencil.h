@@ -235,6 +235,33 @@ stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_t
 stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in, void *out, int64_t steps,
                                    stencil_stream_t stream);
 
+/* Operand layout of the 2:4-structured sparse tensor-core path (Sec. 4.3) at
+ * fusion depth t: the Toeplitz block of each line of w^(t) is the sparse A
+ * operand of mma.sp m16n8k16 TF32 (M = 16 output columns, logical K = 16,
+ * one element kept per pair of logical K).  K is permuted: the 16 + 2R input
+ * columns of the window are cut into 4-column chunks (nc of them) and chunk
+ * pairs (first, second) at least ceil((2R+1)/4) chunks apart are formed;
+ * instruction s takes chunk pairs 2s and 2s+1, its logical pair p being
+ * column 4*chunk + p/2 of chunk pair 2s + (p mod 2). */
+typedef struct {
+    int R;           /* fused radius t*r */
+    int nc;          /* 4-column chunks of the window */
+    int ns;          /* sparse instructions per line (chunk pairs / 2) */
+    int sigma;       /* shared-memory row swizzle of the kernel's B loads */
+    double sparsity; /* S = useful MACs / logical issued MACs */
+} stencil_sptc_layout;
+
+/* The sparse layout of this plan at fusion depth t (host only; FP32 plans,
+ * 2-D, t*r <= 12, else UNSUPPORTED).  chunk_first / chunk_second receive
+ * 2*ns ints (-1 = a dummy chunk); line_mask receives 2R+1 bytes (bit s: line
+ * issues instruction s); values / select receive the compressed A operand,
+ * (2R+1) * ns * 16 * 8 entries at [(line * ns + s) * 128 + m * 8 + p]: the
+ * TF32-rounded weight kept for output column m and logical pair p, and 0 if
+ * it is the pair's first member, 1 if the second.  Any output may be null. */
+stencil_status stencil_plan_sptc_layout(const stencil_plan *plan, int t, stencil_sptc_layout *layout,
+                                        int *chunk_first, int *chunk_second, unsigned char *line_mask,
+                                        float *values, unsigned char *select);
+
 /* One autotuning measurement. */
 typedef struct {
     int path, precision, t;

@@ -57,6 +57,11 @@ class stencil_grid_desc(ctypes.Structure):
                 ("weights", ctypes.POINTER(ctypes.c_double))]
 
 
+class stencil_sptc_layout(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int), ("nc", ctypes.c_int), ("ns", ctypes.c_int), ("sigma", ctypes.c_int),
+                ("sparsity", ctypes.c_double)]
+
+
 class stencil_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("t", ctypes.c_int),
                 ("model_gstencils", ctypes.c_double), ("measured_gstencils", ctypes.c_double)]
@@ -109,6 +114,8 @@ def load() -> ctypes.CDLL:
     L.stencil_run_noalloc.restype = st
     L.stencil_run_host.argtypes = [vp, vp, vp, i64, vp]
     L.stencil_run_host.restype = st
+    L.stencil_plan_sptc_layout.argtypes = [vp, ctypes.c_int, ctypes.POINTER(stencil_sptc_layout), vp, vp, vp, vp, vp]
+    L.stencil_plan_sptc_layout.restype = st
     L.stencil_plan_autotune.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.POINTER(stencil_tune_result),
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.stencil_plan_autotune.restype = st
@@ -252,6 +259,26 @@ def stencil_plan_tc_layout(plan: int, t: int, with_B: bool = True):
 
 def stencil_device_status(stream=None) -> None:
     _check(load().stencil_device_status(_stream_handle(stream)), "stencil_device_status")
+
+
+def stencil_plan_sptc_layout(plan: int, t: int):
+    """Sparse (mma.sp TF32) operand layout: (layout dict, chunk_first, chunk_second,
+    line_mask, values[lines, ns, 16, 8], select[lines, ns, 16, 8])."""
+    import numpy as np
+    lay = stencil_sptc_layout()
+    _check(load().stencil_plan_sptc_layout(plan, t, ctypes.byref(lay), None, None, None, None, None),
+           "stencil_plan_sptc_layout")
+    lines, ns = 2 * lay.R + 1, lay.ns
+    cf = np.zeros(2 * ns, np.int32)
+    cs = np.zeros(2 * ns, np.int32)
+    mask = np.zeros(lines, np.uint8)
+    vals = np.zeros((lines, ns, 16, 8), np.float32)
+    sel = np.zeros((lines, ns, 16, 8), np.uint8)
+    _check(load().stencil_plan_sptc_layout(plan, t, ctypes.byref(lay), cf.ctypes.data, cs.ctypes.data,
+                                           mask.ctypes.data, vals.ctypes.data, sel.ctypes.data),
+           "stencil_plan_sptc_layout")
+    d = {k: getattr(lay, k) for k, _ in stencil_sptc_layout._fields_}
+    return d, cf, cs, mask, vals, sel
 
 
 def stencil_plan_autotune(plan: int, in_ptr: int, out_ptr: int, steps: int, reps: int = 2, stream=None,

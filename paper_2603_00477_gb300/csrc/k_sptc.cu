@@ -1,0 +1,289 @@
+// k_sptc.cu -- the 2:4-structured sparse tensor-core sweep (paper Sec. 4.3):
+// the t-step composite stencil as banded Toeplitz products on the sparse MMA,
+// mma.sp m16n8k16 TF32 (1:2 sparsity of the A operand per pair of K).
+//
+// The Toeplitz block of a line of w^(t) is the sparse A operand (M = 16
+// output columns, logical K = the permuted input window); B is the im2col of
+// the staged input (N = 8 output rows).  The K permutation, the compressed
+// values and their selectors follow sp_layout_2d / sp_a_value, which the
+// dispatcher also uses to report S.
+//
+// CTA: 256 threads, tile 128 output rows x 64 output columns, persistent over
+// tiles; the next tile's input is copied (cp.async) while this one computes,
+// and B fragments are rounded to TF32 in registers after each load.  Warp w owns the 16-column strip w mod 4 and the 64-row band w / 4.
+// Its eight accumulators cover the rows y0 + 8n (y0 = 0..7, n = 0..7) of the
+// band, so the B fragment of input row offset rho = y0 + a (line a) is shared
+// by every (y0, a) with the same sum: a B fragment (one 16-byte shared-memory
+// load per thread) feeds up to eight MMAs of different lines.  The compressed
+// A fragments of all lines are built once per CTA in shared memory and held
+// in registers for a pass of LC lines.
+//
+// Like the dense tensor-core sweeps it writes interior points farther than
+// (t-1) r from the boundary; the CUDA-core band sweep computes the others.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "launch.h"
+#include "tc_layout.h"
+
+namespace gbs {
+
+namespace {
+
+constexpr int kSpMaxLines = 25;
+
+struct SpParams {
+    double w[kSpMaxLines * kSpMaxLines];  // composite w^(t), (2R+1)^2, row-major
+    int cf[2 * kSpMaxNs], cs[2 * kSpMaxNs];
+    unsigned char mask[kSpMaxLines];
+    int R, rh, band, lines, sigma, pitch_q, rl;
+    int64_t Ey, Ex;
+};
+
+__device__ __forceinline__ float cvt_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mma_sp(float (&d)[4], const float4 &a, const float4 &b, uint32_t e)
+{
+    asm volatile(
+        "mma.sp::ordered_metadata.sync.aligned.m16n8k16.row.col.f32.tf32.tf32.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9,%10,%11}, {%0,%1,%2,%3}, %12, 0x0;"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(__float_as_uint(a.x)), "r"(__float_as_uint(a.y)), "r"(__float_as_uint(a.z)), "r"(__float_as_uint(a.w)),
+          "r"(__float_as_uint(b.x)), "r"(__float_as_uint(b.y)), "r"(__float_as_uint(b.z)), "r"(__float_as_uint(b.w)),
+          "r"(e));
+}
+
+__device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src, bool valid)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gmem_src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int kSpTY = 128, kSpTX = 64;
+
+// Fragment layout of mma.sp m16n8k16 TF32 (lane = 4 g + q):
+//   A (16 x 8 compressed): a0 (row g, pair q), a1 (g+8, q), a2 (g, q+4),
+//   a3 (g+8, q+4);  B (16 x 8 logical): b_j = B[q + 4j][g];
+//   D: d0 (g, 2q), d1 (g, 2q+1), d2 (g+8, 2q), d3 (g+8, 2q+1);
+//   selectors (selector 0: lanes with q < 2): lane 4g + h, nibble i ->
+//   (row g, pair 4h + i), nibble 4 + i -> (row g + 8, pair 4h + i);
+//   0x4 keeps the first member of the pair, 0xE the second.
+template <int NS, int LC>
+__global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__ in, float *__restrict__ out,
+                                                       const __grid_constant__ SpParams p, int ntiles, int ntx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int R = p.R, lines = p.lines, PQ = p.pitch_q;
+    float4 *Af = reinterpret_cast<float4 *>(smem_raw);                  // [lines][NS][32]
+    uint32_t *Em = reinterpret_cast<uint32_t *>(Af + lines * NS * 32);  // [lines][NS][32]
+    float *S = reinterpret_cast<float *>(Em + lines * NS * 32);         // two staged tiles
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
+    const int ws = warp & 3, wb = warp >> 2;
+
+    for (int idx = tid; idx < lines * NS * 32; idx += 256) {
+        const int l = idx & 31, blk = idx >> 5, a = blk / NS, s = blk % NS;
+        const int lg = l >> 2, lq = l & 3, hh = lq & 1;
+        int sel;
+        float4 v;
+        v.x = sp_a_value(p.w, R, p.cf, p.cs, a, s, lg, lq, &sel);
+        v.y = sp_a_value(p.w, R, p.cf, p.cs, a, s, lg + 8, lq, &sel);
+        v.z = sp_a_value(p.w, R, p.cf, p.cs, a, s, lg, lq + 4, &sel);
+        v.w = sp_a_value(p.w, R, p.cf, p.cs, a, s, lg + 8, lq + 4, &sel);
+        uint32_t e = 0;
+        for (int i = 0; i < 4; i++) {
+            int s0, s1;
+            sp_a_value(p.w, R, p.cf, p.cs, a, s, lg, 4 * hh + i, &s0);
+            sp_a_value(p.w, R, p.cf, p.cs, a, s, lg + 8, 4 * hh + i, &s1);
+            e |= (s0 ? 0xEu : 0x4u) << (4 * i);
+            e |= (s1 ? 0xEu : 0x4u) << (4 * (i + 4));
+        }
+        Af[idx] = v;
+        Em[idx] = e;
+    }
+
+    // 16-byte chunk (within the warp's strip) of this thread's B registers
+    int bq[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const int cp = 2 * s + (q >> 1);
+        const int c = (q & 1) ? p.cs[cp] : p.cf[cp];
+        bq[s] = 4 * ws + (c < 0 ? 0 : c);
+    }
+    const int H = kSpTY + 2 * R, RL = p.rl;
+    const int64_t ny = p.Ey - 2 * p.rh, nx = p.Ex - 2 * p.rh;
+    const size_t tile_floats = (size_t)H * 4 * PQ;
+
+    // Copy the input tile (rows Y0-R.., columns X0-R.., zero outside the
+    // grid) into a staging buffer with 4-byte asynchronous copies; row i's
+    // 16-byte chunks are XOR-swizzled with sigma when bit 3 of i is set.
+    auto stage = [&](int tile, float *buf) {
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY, X0 = p.rh + (int64_t)tx * kSpTX;
+        for (int i = warp; i < H; i += 8) {
+            const int64_t gy = Y0 - R + i;
+            const bool rok = gy >= 0 && gy < p.Ey;
+            const float *src = in + (rok ? gy : 0) * p.Ex;
+            const int sw = ((i >> 3) & 1) ? p.sigma : 0;
+            float *dst = buf + (size_t)i * 4 * PQ;
+            for (int j = lane; j < RL; j += 32) {
+                const int64_t gx = X0 - R + j;
+                const bool ok = rok && gx >= 0 && gx < p.Ex;
+                cp_async4(dst + 4 * ((j >> 2) ^ sw) + (j & 3), ok ? src + gx : in, ok);
+            }
+        }
+    };
+
+    int cur = 0;
+    if ((int)blockIdx.x < ntiles) stage(blockIdx.x, S);
+    cp_async_commit();
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ty = tile / ntx, tx = tile - ty * ntx;
+        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY, X0 = p.rh + (int64_t)tx * kSpTX;
+        const int nxt = tile + gridDim.x;
+        if (nxt < ntiles) stage(nxt, S + (cur ^ 1) * tile_floats);
+        cp_async_commit();
+        cp_async_wait1();  // this tile's copies have landed (the newest group may still be in flight)
+        __syncthreads();
+        const float *T = S + cur * tile_floats;
+
+        float acc[8][4];
+#pragma unroll
+        for (int y = 0; y < 8; y++) acc[y][0] = acc[y][1] = acc[y][2] = acc[y][3] = 0.0f;
+
+        for (int a_lo = 0; a_lo < lines; a_lo += LC) {
+            const int nl = min(LC, lines - a_lo);
+            float4 A[LC][NS];
+            uint32_t E[LC][NS];
+            unsigned mk[LC];
+#pragma unroll
+            for (int al = 0; al < LC; al++) {
+                mk[al] = al < nl ? p.mask[a_lo + al] : 0u;
+#pragma unroll
+                for (int s = 0; s < NS; s++) {
+                    const int idx = ((a_lo + (al < nl ? al : 0)) * NS + s) * 32 + lane;
+                    A[al][s] = Af[idx];
+                    E[al][s] = Em[idx];
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < LC + 7; rr++) {
+                if (rr >= nl + 7) break;
+                const int row = 64 * wb + a_lo + rr + 8 * g;
+                const int sw = ((row >> 3) & 1) ? p.sigma : 0;
+                const float *srow = T + (size_t)row * 4 * PQ;
+                float4 Bv[NS];
+#pragma unroll
+                for (int s = 0; s < NS; s++) {
+                    Bv[s] = *reinterpret_cast<const float4 *>(srow + 4 * (bq[s] ^ sw));
+                    Bv[s].x = cvt_tf32(Bv[s].x);
+                    Bv[s].y = cvt_tf32(Bv[s].y);
+                    Bv[s].z = cvt_tf32(Bv[s].z);
+                    Bv[s].w = cvt_tf32(Bv[s].w);
+                }
+#pragma unroll
+                for (int y0 = 0; y0 < 8; y0++) {
+                    const int al = rr - y0;
+                    if (al < 0 || al >= LC) continue;
+#pragma unroll
+                    for (int s = 0; s < NS; s++)
+                        if ((mk[al] >> s) & 1u) mma_sp(acc[y0], A[al][s], Bv[s], E[al][s]);
+                }
+            }
+        }
+
+        // epilogue: d0 (col g, row slot 2q), d1 (g, 2q+1), d2 (g+8, 2q), d3 (g+8, 2q+1)
+#pragma unroll
+        for (int y0 = 0; y0 < 8; y0++) {
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const int m = g + 8 * (h >> 1), n = 2 * q + (h & 1);
+                const int64_t gy = Y0 + 64 * wb + y0 + 8 * n, gx = X0 + 16 * ws + m;
+                const int64_t iy = gy - p.rh, ix = gx - p.rh;
+                if (iy < ny && ix < nx && iy >= p.band && ix >= p.band && ny - 1 - iy >= p.band &&
+                    nx - 1 - ix >= p.band)
+                    out[gy * p.Ex + gx] = acc[y0][h];
+            }
+        }
+        __syncthreads();  // every read of this buffer is done before it is refilled
+        cur ^= 1;
+    }
+    cp_async_wait0();
+}
+
+template <int NS, int LC>
+stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t ny, int64_t nx, cudaStream_t st)
+{
+    static int cached = 0;
+    const size_t table = (size_t)sp.lines * NS * 32 * 20;
+    const size_t tile = (size_t)(kSpTY + 2 * sp.R) * sp.pitch_q * 16;
+    const size_t smem = table + 2 * tile;  // double-buffered input tiles
+    if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core tile does not fit in shared memory");
+    auto kern = sptc2d_sweep<NS, LC>;
+    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    if (s != STENCIL_OK) return s;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "sptc2d_sweep occupancy");
+    if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core kernel cannot be resident");
+    const int64_t nty = (ny + kSpTY - 1) / kSpTY, ntx = (nx + kSpTX - 1) / kSpTX, ntiles = nty * ntx;
+    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
+    kern<<<grid, 256, smem, st>>>((const float *)in, (float *)out, sp, (int)ntiles, (int)ntx);
+    note_launch();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "sptc2d_sweep launch");
+}
+
+}  // namespace
+
+stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+{
+    if (p.pat.d != 2 || p.dtype != STENCIL_F32)
+        return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path: 2-D FP32 grids only");
+    const int r = p.pat.r, R = t * r;
+    if (R > 12) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path: fused radius t*r must be <= 12");
+    const SpLayout L = sp_layout_2d(p.pat.shape, r, t);
+    SpParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    const std::vector<double> wt = compose_dense(p.pat, p.w, t);
+    const int lines = 2 * R + 1;
+    for (int i = 0; i < lines * lines; i++) sp.w[i] = wt[i];
+    for (int i = 0; i < 2 * kSpMaxNs; i++) {
+        sp.cf[i] = L.cf[i];
+        sp.cs[i] = L.cs[i];
+    }
+    for (int a = 0; a < lines; a++) sp.mask[a] = (unsigned char)L.mask[a];
+    sp.R = R;
+    sp.rh = r;
+    sp.band = (t - 1) * r;
+    sp.lines = lines;
+    sp.sigma = L.sigma;
+    sp.pitch_q = L.pitch_q;
+    sp.rl = L.rl;
+    sp.Ey = p.ext[1];
+    sp.Ex = p.ext[2];
+    stencil_status s;
+    switch (L.ns) {
+    case 2: s = launch_ns<2, 5>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 3: s = launch_ns<3, 4>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 4: s = launch_ns<4, 3>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    default: return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path: layout");
+    }
+    if (s != STENCIL_OK || t == 1) return s;
+    return launch_cu_band(p, in, out, t, (t - 1) * r, st);
+}
+
+}  // namespace gbs

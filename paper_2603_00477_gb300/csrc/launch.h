@@ -19,6 +19,10 @@ stencil_status launch_cu_band(const Plan &p, const void *in, void *out, int t, i
 // plan's precision form; FP64: FP64 MMA), followed by the band sweep if t > 1.
 stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
 
+// One fused sweep of depth t on the 2:4-structured sparse tensor-core path
+// (mma.sp TF32), followed by the band sweep if t > 1.
+stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
+
 // Read and clear the device error word the tensor-core kernels set when a
 // bounded wait runs out (1 = timed out).
 stencil_status read_device_error(int *flag);

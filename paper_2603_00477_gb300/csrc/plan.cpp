@@ -121,7 +121,16 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
         g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
-    (void)path;
+    if (d == 2 && path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
+        // mma.sp m16n8k16: 16 output columns per block, logical K 16
+        SpLayout L = sp_layout_2d(shape, r, t);
+        g.n_tile = 16;
+        g.k_inst = 16;
+        g.kext = 4 * L.nc;
+        g.sparsity = L.sparsity();
+        g.available = dtype == STENCIL_F32 && precision == STENCIL_PREC_TF32 && t * r <= 12;
+        return g;
+    }
     if (d == 2) {
         TcLines L = tc_lines_2d(shape, r, t, g.n_tile, g.k_inst);
         g.kext = L.kext;
@@ -150,7 +159,10 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
 // FP64 grids on the FP64 MMA, FP32 grids in the TF32 / TF32X3 / BF16X3 forms.
 bool tc_supported(const Plan &p, int precision, int path)
 {
-    if (path != STENCIL_PATH_TENSOR_CORE || p.pat.d != 2) return false;
+    if (p.pat.d != 2) return false;
+    if (path == STENCIL_PATH_SPARSE_TENSOR_CORE)  // mma.sp TF32 (1:2 per pair of K)
+        return p.dtype == STENCIL_F32 && precision == STENCIL_PREC_TF32;
+    if (path != STENCIL_PATH_TENSOR_CORE) return false;
     if (p.dtype == STENCIL_F64) return precision == STENCIL_PREC_NATIVE;
     return precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3;
 }
@@ -249,6 +261,7 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                     c.tile[0] = 1;
                     c.tile[1] = p->dtype == STENCIL_F64 ? 64 : 128;
                     c.tile[2] = p->dtype == STENCIL_F64 ? 64 : (prec == STENCIL_PREC_TF32 ? 64 : (prec == STENCIL_PREC_TF32X3 ? 32 : 64));
+                    if (path == STENCIL_PATH_SPARSE_TENSOR_CORE) c.tile[2] = 64;
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec), P_cu,
                                             tc_peak(*p, prec, path), B);
@@ -506,6 +519,44 @@ stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_t
                     for (int n = 0; n < L.n_tile; n++) {
                         const int b = kb * L.k_inst + k - n - L.R;
                         B[i++] = (b >= -L.R && b <= L.R) ? wt[(size_t)a * lines + (b + L.R)] : 0.0;
+                    }
+    }
+    return STENCIL_OK;
+}
+
+stencil_status stencil_plan_sptc_layout(const stencil_plan *plan, int t, stencil_sptc_layout *layout,
+                                        int *chunk_first, int *chunk_second, unsigned char *line_mask,
+                                        float *values, unsigned char *select)
+{
+    if (!plan || !layout) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_sptc_layout: null argument");
+    const Plan &p = plan->p;
+    if (t < 1 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_sptc_layout: t must be 1..16");
+    if (p.pat.d != 2 || p.dtype != STENCIL_F32 || t * p.pat.r > 12)
+        return fail(STENCIL_ERR_UNSUPPORTED, "stencil_plan_sptc_layout: no sparse kernel for this plan and t");
+    const SpLayout L = sp_layout_2d(p.pat.shape, p.pat.r, t);
+    layout->R = L.R;
+    layout->nc = L.nc;
+    layout->ns = L.ns;
+    layout->sigma = L.sigma;
+    layout->sparsity = L.sparsity();
+    for (int i = 0; i < 2 * L.ns; i++) {
+        if (chunk_first) chunk_first[i] = L.cf[i];
+        if (chunk_second) chunk_second[i] = L.cs[i];
+    }
+    const int lines = 2 * L.R + 1;
+    for (int a = 0; a < lines; a++)
+        if (line_mask) line_mask[a] = (unsigned char)L.mask[a];
+    if (values || select) {
+        const std::vector<double> wt = compose_dense(p.pat, p.w, t);
+        size_t i = 0;
+        for (int a = 0; a < lines; a++)
+            for (int s = 0; s < L.ns; s++)
+                for (int m = 0; m < 16; m++)
+                    for (int q = 0; q < 8; q++, i++) {
+                        int sel = 0;
+                        const float v = sp_a_value(wt.data(), L.R, L.cf, L.cs, a, s, m, q, &sel);
+                        if (values) values[i] = v;
+                        if (select) select[i] = (unsigned char)sel;
                     }
     }
     return STENCIL_OK;

@@ -96,7 +96,7 @@ static stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, s
         } else if (p.path == STENCIL_PATH_TENSOR_CORE) {
             s = launch_tc_sweep(p, src, dst, tk, st);
         } else {
-            s = fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path not built");
+            s = launch_sptc_sweep(p, src, dst, tk, st);
         }
         if (s != STENCIL_OK) return s;
         src = dst;

@@ -85,4 +85,142 @@ inline int tc_ws_ntile(int shape, int r, int t, bool split)
     return 8;
 }
 
+// ---------------------------------------------------------------------------
+// 2:4-structured sparse form (paper Sec. 4.3), TF32 1:2 on mma.sp m16n8k16.
+//
+// The sparse operand must be A, so the Toeplitz block of line a is the A
+// operand: A_a[m][k] = w^(t)[a][k - m] (0 <= k - m <= 2R) with M = 16 output
+// columns and K = the 16 + 2R input columns of the window; B is the im2col
+// of the input (K x 8 output rows).  TF32 sparsity keeps one element of every
+// pair of consecutive logical K positions, so K is permuted ("strided
+// swapping"): the window is cut into 16-byte chunks (4 columns) and chunk c is
+// paired with a chunk at least ceil((2R+1)/4) chunks away, so no row's band
+// holds both members of a pair.  Instruction s takes the chunk pairs 2s and
+// 2s+1; its logical pair p is element p/2 of chunk pair 2s + (p mod 2).  A
+// chunk index of -1 is a dummy (zero operand).
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+#define GBS_HD __host__ __device__ __forceinline__
+#else
+#define GBS_HD inline
+#endif
+
+constexpr int kSpMaxNs = 4;  // instructions per line (R <= 12)
+
+struct SpLayout {
+    int R = 0, nc = 0, ns = 0, sigma = 0, pitch_q = 0, rl = 0;
+    int cf[2 * kSpMaxNs], cs[2 * kSpMaxNs];  // chunk pairs (first, second); -1 = dummy
+    std::vector<int> mask;                   // per line: bit s = instruction s issued
+    double useful = 0, issued = 0;           // per output point (issued: logical K)
+    double sparsity() const { return issued > 0 ? useful / issued : 0.0; }
+};
+
+// Round an FP32 value to TF32 (nearest, ties away from zero), as the
+// conversion instruction does for finite values.
+GBS_HD float tf32_round(float x)
+{
+    union {
+        float f;
+        unsigned u;
+    } v;
+    v.f = x;
+    v.u = (v.u + 0x1000u) & 0xFFFFE000u;
+    return v.f;
+}
+
+// Value and selector (0: first, 1: second member) of compressed A element
+// (row m, logical pair p) of instruction s for line a.  w: the composite
+// kernel, (2R+1) x (2R+1) row-major.
+GBS_HD float sp_a_value(const double *w, int R, const int *cf, const int *cs, int a, int s, int m, int p,
+                        int *sel)
+{
+    const int cp = 2 * s + (p & 1), i = p >> 1, lines = 2 * R + 1;
+    const int fc = cf[cp], sc = cs[cp];
+    *sel = 0;
+    if (fc >= 0) {
+        const int b = 4 * fc + i - m;
+        if (b >= 0 && b <= 2 * R && w[a * lines + b] != 0.0) return tf32_round((float)w[a * lines + b]);
+    }
+    if (sc >= 0) {
+        const int b = 4 * sc + i - m;
+        if (b >= 0 && b <= 2 * R && w[a * lines + b] != 0.0) {
+            *sel = 1;
+            return tf32_round((float)w[a * lines + b]);
+        }
+    }
+    return 0.0f;
+}
+
+inline SpLayout sp_layout_2d(int shape, int r, int t)
+{
+    SpLayout L;
+    const int R = t * r;
+    L.R = R;
+    L.nc = (16 + 2 * R + 3) / 4;
+    const int dc = (2 * R + 1 + 3) / 4;  // minimum chunk distance of a pair
+    std::vector<int> pf, ps, used(L.nc, 0);
+    for (int c = 0; c < L.nc; c++) {
+        if (used[c]) continue;
+        used[c] = 1;
+        int partner = -1;
+        for (int c2 = c + dc; c2 < L.nc; c2++)
+            if (!used[c2]) {
+                partner = c2;
+                used[c2] = 1;
+                break;
+            }
+        pf.push_back(c);
+        ps.push_back(partner);
+    }
+    L.ns = ((int)pf.size() + 1) / 2;
+    for (int i = 0; i < 2 * kSpMaxNs; i++) {
+        L.cf[i] = i < (int)pf.size() ? pf[i] : -1;
+        L.cs[i] = i < (int)ps.size() ? ps[i] : -1;
+    }
+    // row swizzle: rows 8 apart XOR their 16-byte chunk index with sigma so
+    // that the two rows of one quarter-warp's 16-byte loads hit disjoint banks
+    int best = 1 << 30;
+    for (int sg = 0; sg < 8; sg++) {
+        int conflicts = 0;
+        for (int s = 0; s < L.ns; s++) {
+            int cnt[8] = {0};
+            const int q[4] = {L.cf[2 * s], L.cs[2 * s], L.cf[2 * s + 1], L.cs[2 * s + 1]};
+            for (int j = 0; j < 4; j++) {
+                const int c = q[j] < 0 ? 0 : q[j];
+                cnt[c & 7]++;
+                cnt[(c & 7) ^ sg]++;
+            }
+            for (int b = 0; b < 8; b++) conflicts += cnt[b] > 1 ? cnt[b] - 1 : 0;
+        }
+        if (conflicts < best) {
+            best = conflicts;
+            L.sigma = sg;
+        }
+    }
+    L.rl = 48 + 4 * L.nc;                 // staged row: 3 strips of 16 + the last window
+    L.pitch_q = (L.rl / 4 + 7) / 8 * 8;  // 16-byte chunks per row, multiple of 8
+    for (int a = -R; a <= R; a++) {
+        const int h = composite_half(shape, r, t, a);
+        int m = 0;
+        if (h >= 0) {
+            // non-zero columns of the line over the 16 rows: [R-h, R+h+15]
+            for (int s = 0; s < L.ns; s++) {
+                bool hit = false;
+                for (int j = 0; j < 2; j++) {
+                    const int cp = 2 * s + j;
+                    for (int c : {L.cf[cp], L.cs[cp]}) {
+                        if (c < 0) continue;
+                        if (4 * c + 3 >= R - h && 4 * c <= R + h + 15) hit = true;
+                    }
+                }
+                if (hit) m |= 1 << s;
+            }
+            L.useful += 2 * h + 1;
+            L.issued += 16.0 * __builtin_popcount((unsigned)m);
+        }
+        L.mask.push_back(m);
+    }
+    return L;
+}
+
 }  // namespace gbs

@@ -58,7 +58,7 @@ def test_autotune_picks_fastest_and_runs_it(torch, shape, r, dtype, prec):
 def test_autotune_rejects_bad_arguments(torch):
     w = inputs.weights("box", 2, 1, seed=1)
     plan = B.Plan("box", 2, 1, w, "f64", (64, 64))
-    x = torch.zeros(plan.stored_shape(), dtype=torch.float64, device="cuda")
+    x = torch.zeros(plan.stored_shape, dtype=torch.float64, device="cuda")
     with pytest.raises(B.StencilError) as e:
         B.stencil_plan_autotune(plan.handle, x.data_ptr(), x.data_ptr(), 0)
     assert e.value.status == B.STENCIL_ERR_INVALID_ARG
