@@ -36,9 +36,9 @@ constexpr int kSpMaxLines = 25;
 
 struct SpParams {
     double w[kSpMaxLines * kSpMaxLines];  // composite w^(t), (2R+1)^2, row-major
-    int cf[2 * kSpMaxNs], cs[2 * kSpMaxNs];
+    int cf[2 * kSpMaxNs], cs[2 * kSpMaxNs], bchunk[4 * kSpMaxNs];
     unsigned char mask[kSpMaxLines];
-    int R, rh, band, lines, sigma, pitch_q, rl;
+    int R, rh, band, lines, sigma, pitch_q, rl, nbuf;
     int64_t Ey, Ex;
 };
 
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
     const int R = p.R, lines = p.lines, PQ = p.pitch_q;
     float4 *Af = reinterpret_cast<float4 *>(smem_raw);                  // [lines][NS][32]
     uint32_t *Em = reinterpret_cast<uint32_t *>(Af + lines * NS * 32);  // [lines][NS][32]
-    float *S = reinterpret_cast<float *>(Em + lines * NS * 32);         // two staged tiles
+    float *S = reinterpret_cast<float *>(Em + lines * NS * 32);         // one or two staged tiles
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, q = lane & 3;
     const int ws = warp & 3, wb = warp >> 2;
 
@@ -112,55 +112,76 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
         Em[idx] = e;
     }
 
-    // 16-byte chunk (within the warp's strip) of this thread's B registers
-    int bq[NS];
+    // B offsets (floats within a staged row) of this thread, for a row whose
+    // chunks are not swizzled (0) and swizzled (1)
+    int boff0[NS], boff1[NS];
 #pragma unroll
     for (int s = 0; s < NS; s++) {
-        const int cp = 2 * s + (q >> 1);
-        const int c = (q & 1) ? p.cs[cp] : p.cf[cp];
-        bq[s] = 4 * ws + (c < 0 ? 0 : c);
+        const int c = 4 * ws + p.bchunk[4 * s + q];
+        boff0[s] = 4 * c;
+        boff1[s] = 4 * (c ^ p.sigma);
     }
-    const int H = kSpTY + 2 * R, RL = p.rl;
-    const int64_t ny = p.Ey - 2 * p.rh, nx = p.Ex - 2 * p.rh;
-    const size_t tile_floats = (size_t)H * 4 * PQ;
+    const int H = kSpTY + 2 * R, RL = p.rl, RP = 4 * PQ;
+    const int64_t ny = p.Ey - 2 * p.rh, nx = p.Ex - 2 * p.rh, Ex = p.Ex;
+    const size_t tile_floats = (size_t)H * RP;
+    const bool dbl = p.nbuf == 2;
 
-    // Copy the input tile (rows Y0-R.., columns X0-R.., zero outside the
-    // grid) into a staging buffer with 4-byte asynchronous copies; row i's
-    // 16-byte chunks are XOR-swizzled with sigma when bit 3 of i is set.
+    // Each thread copies (and later rounds) the same elements of every tile:
+    // rows warp + 8i, columns lane + 32k of the staged window.
     auto stage = [&](int tile, float *buf) {
         const int ty = tile / ntx, tx = tile - ty * ntx;
-        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY, X0 = p.rh + (int64_t)tx * kSpTX;
+        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY - R, X0 = p.rh + (int64_t)tx * kSpTX - R;
+        const bool inside = Y0 >= 0 && Y0 + H <= p.Ey && X0 >= 0 && X0 + RL <= Ex;
         for (int i = warp; i < H; i += 8) {
-            const int64_t gy = Y0 - R + i;
-            const bool rok = gy >= 0 && gy < p.Ey;
-            const float *src = in + (rok ? gy : 0) * p.Ex;
             const int sw = ((i >> 3) & 1) ? p.sigma : 0;
-            float *dst = buf + (size_t)i * 4 * PQ;
-            for (int j = lane; j < RL; j += 32) {
-                const int64_t gx = X0 - R + j;
-                const bool ok = rok && gx >= 0 && gx < p.Ex;
-                cp_async4(dst + 4 * ((j >> 2) ^ sw) + (j & 3), ok ? src + gx : in, ok);
+            float *dst = buf + (size_t)i * RP + 4 * ((lane >> 2) ^ sw) + (lane & 3);
+            const int64_t gy = Y0 + i;
+            if (inside) {
+                const float *src = in + gy * Ex + X0 + lane;
+                for (int j = 0; j + lane < RL; j += 32) cp_async4(dst + j, src + j, true);
+            } else {
+                const bool rok = gy >= 0 && gy < p.Ey;
+                for (int j = 0; j + lane < RL; j += 32) {
+                    const int64_t gx = X0 + lane + j;
+                    const bool ok = rok && gx >= 0 && gx < Ex;
+                    cp_async4(dst + j, ok ? in + gy * Ex + gx : in, ok);
+                }
             }
+        }
+    };
+    auto round_own = [&](float *buf) {
+        for (int i = warp; i < H; i += 8) {
+            const int sw = ((i >> 3) & 1) ? p.sigma : 0;
+            float *dst = buf + (size_t)i * RP + 4 * ((lane >> 2) ^ sw) + (lane & 3);
+            for (int j = 0; j + lane < RL; j += 32) dst[j] = cvt_tf32(dst[j]);
         }
     };
 
     int cur = 0;
-    if ((int)blockIdx.x < ntiles) stage(blockIdx.x, S);
+    if (dbl && (int)blockIdx.x < ntiles) stage(blockIdx.x, S);
     cp_async_commit();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ty = tile / ntx, tx = tile - ty * ntx;
         const int64_t Y0 = p.rh + (int64_t)ty * kSpTY, X0 = p.rh + (int64_t)tx * kSpTX;
-        const int nxt = tile + gridDim.x;
-        if (nxt < ntiles) stage(nxt, S + (cur ^ 1) * tile_floats);
-        cp_async_commit();
-        cp_async_wait1();  // this tile's copies have landed (the newest group may still be in flight)
+        float *T = S + cur * tile_floats;
+        if (dbl) {
+            const int nxt = tile + gridDim.x;
+            if (nxt < ntiles) stage(nxt, S + (cur ^ 1) * tile_floats);
+            cp_async_commit();
+            cp_async_wait1();  // this tile's copies have landed (the newest group may still be in flight)
+        } else {
+            stage(tile, T);
+            cp_async_commit();
+            cp_async_wait0();
+        }
+        round_own(T);
         __syncthreads();
-        const float *T = S + cur * tile_floats;
 
         float acc[8][4];
 #pragma unroll
         for (int y = 0; y < 8; y++) acc[y][0] = acc[y][1] = acc[y][2] = acc[y][3] = 0.0f;
 
+        const float *Tw = T + (size_t)(64 * wb + 8 * g) * RP;
         for (int a_lo = 0; a_lo < lines; a_lo += LC) {
             const int nl = min(LC, lines - a_lo);
             float4 A[LC][NS];
@@ -179,44 +200,54 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
 #pragma unroll
             for (int rr = 0; rr < LC + 7; rr++) {
                 if (rr >= nl + 7) break;
-                const int row = 64 * wb + a_lo + rr + 8 * g;
-                const int sw = ((row >> 3) & 1) ? p.sigma : 0;
-                const float *srow = T + (size_t)row * 4 * PQ;
+                const int rho = a_lo + rr;  // input row offset of the band (+ 8 g)
+                const int swz = ((rho >> 3) ^ g) & 1;
+                const float *srow = Tw + (size_t)rho * RP;
                 float4 Bv[NS];
 #pragma unroll
+                for (int s = 0; s < NS; s++)
+                    Bv[s] = *reinterpret_cast<const float4 *>(srow + (swz ? boff1[s] : boff0[s]));
+#pragma unroll
                 for (int s = 0; s < NS; s++) {
-                    Bv[s] = *reinterpret_cast<const float4 *>(srow + 4 * (bq[s] ^ sw));
-                    Bv[s].x = cvt_tf32(Bv[s].x);
-                    Bv[s].y = cvt_tf32(Bv[s].y);
-                    Bv[s].z = cvt_tf32(Bv[s].z);
-                    Bv[s].w = cvt_tf32(Bv[s].w);
-                }
 #pragma unroll
-                for (int y0 = 0; y0 < 8; y0++) {
-                    const int al = rr - y0;
-                    if (al < 0 || al >= LC) continue;
-#pragma unroll
-                    for (int s = 0; s < NS; s++)
+                    for (int y0 = 0; y0 < 8; y0++) {
+                        const int al = rr - y0;
+                        if (al < 0 || al >= LC) continue;
                         if ((mk[al] >> s) & 1u) mma_sp(acc[y0], A[al][s], Bv[s], E[al][s]);
+                    }
                 }
             }
         }
 
-        // epilogue: d0 (col g, row slot 2q), d1 (g, 2q+1), d2 (g+8, 2q), d3 (g+8, 2q+1)
+        // epilogue: d0 (col g, row slot 2q), d1 (g, 2q+1), d2 (g+8, 2q), d3 (g+8, 2q+1);
+        // row slot n of accumulator y0 is output row y0 + 8n of the band
+        const int64_t by = Y0 + 64 * wb, bx = X0 + 16 * ws;
+        const int64_t iy0 = by - p.rh, ix0 = bx - p.rh;
+        const bool full = iy0 >= p.band && ix0 >= p.band && iy0 + 64 <= ny - p.band && ix0 + 16 <= nx - p.band;
+        float *ob = out + (by + 16 * q) * Ex + bx + g;
+        if (full) {
 #pragma unroll
-        for (int y0 = 0; y0 < 8; y0++) {
+            for (int y0 = 0; y0 < 8; y0++) {
+                ob[y0 * Ex] = acc[y0][0];
+                ob[(y0 + 8) * Ex] = acc[y0][1];
+                ob[y0 * Ex + 8] = acc[y0][2];
+                ob[(y0 + 8) * Ex + 8] = acc[y0][3];
+            }
+        } else {
 #pragma unroll
-            for (int h = 0; h < 4; h++) {
-                const int m = g + 8 * (h >> 1), n = 2 * q + (h & 1);
-                const int64_t gy = Y0 + 64 * wb + y0 + 8 * n, gx = X0 + 16 * ws + m;
-                const int64_t iy = gy - p.rh, ix = gx - p.rh;
-                if (iy < ny && ix < nx && iy >= p.band && ix >= p.band && ny - 1 - iy >= p.band &&
-                    nx - 1 - ix >= p.band)
-                    out[gy * p.Ex + gx] = acc[y0][h];
+            for (int y0 = 0; y0 < 8; y0++) {
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const int m = g + 8 * (h >> 1), n = 2 * q + (h & 1);
+                    const int64_t iy = iy0 + y0 + 8 * n, ix = ix0 + m;
+                    if (iy < ny && ix < nx && iy >= p.band && ix >= p.band && ny - 1 - iy >= p.band &&
+                        nx - 1 - ix >= p.band)
+                        out[(iy + p.rh) * Ex + ix + p.rh] = acc[y0][h];
+                }
             }
         }
         __syncthreads();  // every read of this buffer is done before it is refilled
-        cur ^= 1;
+        if (dbl) cur ^= 1;
     }
     cp_async_wait0();
 }
@@ -227,7 +258,11 @@ stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t 
     static int cached = 0;
     const size_t table = (size_t)sp.lines * NS * 32 * 20;
     const size_t tile = (size_t)(kSpTY + 2 * sp.R) * sp.pitch_q * 16;
-    const size_t smem = table + 2 * tile;  // double-buffered input tiles
+    // double-buffered input tiles when two CTAs still fit on an SM, else one
+    // buffer (the second CTA's copies overlap this one's MMAs)
+    SpParams sp2 = sp;
+    sp2.nbuf = table + 2 * tile <= 112 * 1024 ? 2 : 1;
+    const size_t smem = table + sp2.nbuf * tile;
     if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core tile does not fit in shared memory");
     auto kern = sptc2d_sweep<NS, LC>;
     stencil_status s = ensure_smem((const void *)kern, smem, &cached);
@@ -241,7 +276,7 @@ stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t 
     const int64_t nty = (ny + kSpTY - 1) / kSpTY, ntx = (nx + kSpTX - 1) / kSpTX, ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
-    kern<<<grid, 256, smem, st>>>((const float *)in, (float *)out, sp, (int)ntiles, (int)ntx);
+    kern<<<grid, 256, smem, st>>>((const float *)in, (float *)out, sp2, (int)ntiles, (int)ntx);
     note_launch();
     e = cudaGetLastError();
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "sptc2d_sweep launch");
@@ -265,6 +300,7 @@ stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t
         sp.cf[i] = L.cf[i];
         sp.cs[i] = L.cs[i];
     }
+    for (int i = 0; i < 4 * kSpMaxNs; i++) sp.bchunk[i] = i < 4 * L.ns ? L.bchunk[i] : 0;
     for (int a = 0; a < lines; a++) sp.mask[a] = (unsigned char)L.mask[a];
     sp.R = R;
     sp.rh = r;

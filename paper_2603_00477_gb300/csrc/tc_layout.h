@@ -110,6 +110,8 @@ constexpr int kSpMaxNs = 4;  // instructions per line (R <= 12)
 struct SpLayout {
     int R = 0, nc = 0, ns = 0, sigma = 0, pitch_q = 0, rl = 0;
     int cf[2 * kSpMaxNs], cs[2 * kSpMaxNs];  // chunk pairs (first, second); -1 = dummy
+    int bchunk[4 * kSpMaxNs];                // chunk each lane class q of instruction s loads B from
+                                             // (a dummy gets a filler chunk; its A is zero)
     std::vector<int> mask;                   // per line: bit s = instruction s issued
     double useful = 0, issued = 0;           // per output point (issued: logical K)
     double sparsity() const { return issued > 0 ? useful / issued : 0.0; }
@@ -177,24 +179,49 @@ inline SpLayout sp_layout_2d(int shape, int r, int t)
         L.cf[i] = i < (int)pf.size() ? pf[i] : -1;
         L.cs[i] = i < (int)ps.size() ? ps[i] : -1;
     }
-    // row swizzle: rows 8 apart XOR their 16-byte chunk index with sigma so
-    // that the two rows of one quarter-warp's 16-byte loads hit disjoint banks
+    // B chunk of lane class q (0..3) of instruction s: first / second member
+    // of chunk pair 2s + q/2.  Rows 8 apart XOR their 16-byte chunk index
+    // with sigma; sigma and the filler chunks of dummies are chosen so that
+    // the eight 16-byte loads of a quarter warp (two rows, four chunks) hit
+    // eight distinct bank groups where possible.
     int best = 1 << 30;
     for (int sg = 0; sg < 8; sg++) {
-        int conflicts = 0;
+        int total = 0, pick[4 * kSpMaxNs];
         for (int s = 0; s < L.ns; s++) {
-            int cnt[8] = {0};
-            const int q[4] = {L.cf[2 * s], L.cs[2 * s], L.cf[2 * s + 1], L.cs[2 * s + 1]};
-            for (int j = 0; j < 4; j++) {
-                const int c = q[j] < 0 ? 0 : q[j];
-                cnt[c & 7]++;
-                cnt[(c & 7) ^ sg]++;
+            const int fixed[4] = {L.cf[2 * s], L.cs[2 * s], L.cf[2 * s + 1], L.cs[2 * s + 1]};
+            int bestc = 1 << 30, choice[4] = {0, 0, 0, 0};
+            // enumerate fillers for the dummy slots (nc <= 10 choices each)
+            int slots[4], nd = 0;
+            for (int j = 0; j < 4; j++)
+                if (fixed[j] < 0) slots[nd++] = j;
+            int combos = 1;
+            for (int j = 0; j < nd; j++) combos *= L.nc;
+            for (int cidx = 0; cidx < combos; cidx++) {
+                int c[4], v = cidx;
+                for (int j = 0; j < 4; j++) c[j] = fixed[j];
+                for (int j = 0; j < nd; j++) {
+                    c[slots[j]] = v % L.nc;
+                    v /= L.nc;
+                }
+                int cnt[8] = {0};
+                for (int j = 0; j < 4; j++) {
+                    cnt[c[j] & 7]++;
+                    cnt[(c[j] & 7) ^ sg]++;
+                }
+                int conf = 0;
+                for (int b = 0; b < 8; b++) conf += cnt[b] > 1 ? cnt[b] - 1 : 0;
+                if (conf < bestc) {
+                    bestc = conf;
+                    for (int j = 0; j < 4; j++) choice[j] = c[j];
+                }
             }
-            for (int b = 0; b < 8; b++) conflicts += cnt[b] > 1 ? cnt[b] - 1 : 0;
+            total += bestc;
+            for (int j = 0; j < 4; j++) pick[4 * s + j] = choice[j];
         }
-        if (conflicts < best) {
-            best = conflicts;
+        if (total < best) {
+            best = total;
             L.sigma = sg;
+            for (int i = 0; i < 4 * L.ns; i++) L.bchunk[i] = pick[i];
         }
     }
     L.rl = 48 + 4 * L.nc;                 // staged row: 3 strips of 16 + the last window
