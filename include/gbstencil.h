@@ -333,13 +333,49 @@ stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *
  * up a dependency wait (its outputs are then incomplete). */
 stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t stream);
 
-/* Batch options (integer values):
+/* Batch options:
+ *   "precision"          native | tf32 | tf32x3 | bf16x3 | any: the forms the
+ *                        autotuner may give FP32 grids on tensor cores
+ *                        (default native: CUDA cores only)
+ *   "path"               auto | cuda_core | tensor_core | sparse_tensor_core:
+ *                        put every grid on this path (its model-chosen form
+ *                        and t); grids on a tensor-core path run as their own
+ *                        sweeps after the persistent kernel, in the same graph
+ * and, with integer values:
  *   "wait_cycles"        limit of each dependency wait in SM clock cycles
  *                        (default 2^31, about one second)
  *   "debug_block_sweep"  test hook: items of this sweep (>= 1) wait on a
  *                        counter nothing increments, so the wait runs out and
  *                        the launch aborts; -1 switches it off (default). */
 stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, const char *value);
+
+/* One measured candidate of the batched autotuner. */
+typedef struct {
+    int cls;          /* class index (classes ordered by shape, radius, size) */
+    int shape, r;     /* the class's stencil                                   */
+    int size_class;   /* interior points in [4^(6+c), 4^(7+c)): side ~ 64*2^c  */
+    int ngrids;       /* grids in the class                                    */
+    int path, precision, t, tile_y, tile_x;
+    double model_gstencils;     /* the model's prediction (class's first grid) */
+    double measured_gstencils;  /* class points * steps / s / 1e9; 0 = not run */
+    int chosen;                 /* 1 for the class's winner                    */
+} stencil_batch_tune_result;
+
+/* Autotuner of the batched form, seeded by the model: groups the grids into
+ * shape classes (stencil shape, radius, size class), ranks each class's
+ * candidates -- CUDA-core work items (t = 1..4, tiles 16x64 .. 128x128) and,
+ * for size classes >= 3 when the batch precision allows (FP64 batches, or
+ * FP32 with precision other than "native"), the dense and sparse
+ * tensor-core paths (t = 1..4) -- by the model, measures the model's best
+ * four of each path and the current choice on the class's grids alone (`reps` timed runs of
+ * `steps` steps after one untimed run, CUDA events on `stream`, inputs
+ * ins/outs as for stencil_batch_run; outputs are overwritten), and gives every
+ * grid of the class the fastest.  Writes up to max_results rows (results may
+ * be null) and their count to *n_results.  The workspace a run needs may
+ * change: query stencil_batch_workspace_bytes again.  Synchronises `stream`. */
+stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *ins, void *const *outs,
+                                      int64_t steps, int reps, stencil_stream_t stream,
+                                      stencil_batch_tune_result *results, int max_results, int *n_results);
 
 void stencil_batch_destroy(stencil_batch *batch);
 

@@ -62,6 +62,13 @@ class stencil_sptc_layout(ctypes.Structure):
                 ("sparsity", ctypes.c_double)]
 
 
+class stencil_batch_tune_result(ctypes.Structure):
+    _fields_ = [("cls", ctypes.c_int), ("shape", ctypes.c_int), ("r", ctypes.c_int), ("size_class", ctypes.c_int),
+                ("ngrids", ctypes.c_int), ("path", ctypes.c_int), ("precision", ctypes.c_int), ("t", ctypes.c_int),
+                ("tile_y", ctypes.c_int), ("tile_x", ctypes.c_int), ("model_gstencils", ctypes.c_double),
+                ("measured_gstencils", ctypes.c_double), ("chosen", ctypes.c_int)]
+
+
 class stencil_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("t", ctypes.c_int),
                 ("model_gstencils", ctypes.c_double), ("measured_gstencils", ctypes.c_double)]
@@ -153,6 +160,9 @@ def load() -> ctypes.CDLL:
     L.stencil_batch_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_char_p]
     L.stencil_batch_set_option.restype = st
     L.stencil_batch_destroy.argtypes = [vp]
+    L.stencil_batch_autotune.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.POINTER(stencil_batch_tune_result),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.stencil_batch_autotune.restype = st
     L.stencil_batch_destroy.restype = None
     L.stencil_status_string.argtypes = [ctypes.c_int]
     L.stencil_status_string.restype = ctypes.c_char_p
@@ -477,6 +487,24 @@ def stencil_batch_set_option(batch: int, key: str, value) -> None:
            f"stencil_batch_set_option({key})")
 
 
+def stencil_batch_autotune(batch: int, in_ptrs, out_ptrs, steps: int, reps: int = 1, stream=None,
+                           max_results: int = 2048) -> list:
+    res = (stencil_batch_tune_result * max_results)()
+    n = ctypes.c_int(0)
+    _check(load().stencil_batch_autotune(batch, _ptr_array(in_ptrs), _ptr_array(out_ptrs), int(steps), int(reps),
+                                         _stream_handle(stream), res, max_results, ctypes.byref(n)),
+           "stencil_batch_autotune")
+    out = []
+    for q in res[:min(n.value, max_results)]:
+        d = {f: getattr(q, f) for f, _ in stencil_batch_tune_result._fields_}
+        d["shape"] = "box" if q.shape == 0 else "star"
+        d["path"] = PATH_NAMES[q.path]
+        d["precision"] = PREC_NAMES[q.precision]
+        d["chosen"] = bool(q.chosen)
+        out.append(d)
+    return out
+
+
 def stencil_batch_destroy(batch: int) -> None:
     if batch:
         load().stencil_batch_destroy(batch)
@@ -506,6 +534,16 @@ class Batch:
             self._ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
             stencil_batch_set_workspace(self.handle, self._ws.data_ptr(), self._ws.numel())
         return self._ws
+
+    def set_option(self, key, value):
+        stencil_batch_set_option(self.handle, key, value)
+
+    def autotune(self, ins, outs, steps: int, reps: int = 1, stream=None) -> list:
+        """Tune (path, t, tile) per shape class on these buffers (outputs are
+        overwritten); the next run re-sizes the workspace if it must."""
+        self.ensure_workspace(steps, ins[0].device)
+        return stencil_batch_autotune(self.handle, [x.data_ptr() for x in ins], [y.data_ptr() for y in outs], steps,
+                                      reps, stream)
 
     def run(self, ins, outs, steps: int, stream=None, graph: bool = False):
         self.ensure_workspace(steps, ins[0].device)

@@ -14,8 +14,10 @@
 // nearest to their tile from `in` to the grid's output and ping-pong buffers.
 // On a wait that runs out, the CTA sets the abort word and every CTA leaves.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -245,13 +247,18 @@ __global__ void __launch_bounds__(kThreads)
 // host side
 // ---------------------------------------------------------------------------
 struct BatchGridHost {
-    Plan plan;  // pattern, weights, t and tile chosen by the CUDA-core dispatch
+    Plan plan;  // pattern, weights, path, precision, t and tile
+    // CUDA-core grids run as work items of the persistent kernel; a grid on a
+    // tensor-core path runs as the plan's own sweeps after it, on the same
+    // stream (and inside the same graph)
+    bool on_cu() const { return plan.path == STENCIL_PATH_CUDA_CORE; }
 };
 
 struct BatchCache {
     std::vector<const void *> ins;
     std::vector<void *> outs;
     int64_t steps = -1;
+    size_t kernel_nodes = 1;
     void *ws = nullptr;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -269,6 +276,7 @@ struct stencil_batch {
     bool ran = false;
     unsigned long long wait_cycles = gbs::bt::kWaitCycles;  // bounded dependency wait
     int block_sweep = -1;  // test hook: sweep whose items wait on a counter nothing increments
+    int precision = STENCIL_PREC_NATIVE;  // forms the autotuner may use for FP32 grids
     gbs::BatchCache cache;
 };
 
@@ -297,7 +305,7 @@ Layout layout_of(const stencil_batch &b, int64_t steps)
     int64_t nitems = 0, ndone = 0, nw = 0;
     for (auto &g : b.grids) {
         const int ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
-        nitems += ntiles_of(g.plan) * ns;
+        if (g.on_cu()) nitems += ntiles_of(g.plan) * ns;
         ndone += ns;
         nw += g.plan.pat.K;
     }
@@ -328,15 +336,34 @@ Layout layout_of(const stencil_batch &b, int64_t steps)
     return L;
 }
 
-stencil_status launch_batch(stencil_batch *b, const Layout &L, cudaStream_t st, bool count)
+// Grids on a tensor-core path: each runs its plan's sweeps (ping-pong
+// through its buffer in the workspace).
+stencil_status launch_tc_grids(stencil_batch *b, const Layout &L, const void *const *ins, void *const *outs,
+                               int64_t steps, cudaStream_t st)
+{
+    for (size_t i = 0; i < b->grids.size(); i++) {
+        BatchGridHost &g = b->grids[i];
+        if (g.on_cu()) continue;
+        void *pp = L.pp_of[i] == SIZE_MAX ? nullptr : (char *)b->ws + L.pp_of[i];
+        stencil_status s = run_sweeps(g.plan, ins[i], outs[i], pp, pp ? g.plan.grid_bytes() : 0, steps, st);
+        if (s != STENCIL_OK) return s;
+    }
+    return STENCIL_OK;
+}
+
+stencil_status launch_batch(stencil_batch *b, const Layout &L, const void *const *ins, void *const *outs,
+                            int64_t steps, cudaStream_t st, bool count)
 {
     char *ws = (char *)b->ws;
     cudaError_t e = cudaMemsetAsync(ws + L.done_off, 0, L.ctl_off - L.done_off + sizeof(bt::Ctl), st);
     if (e != cudaSuccess) return cuda_fail(e, "batch: clearing the counters");
-    if (L.nitems == 0) return STENCIL_OK;
+    b->ctl_off = L.ctl_off;
+    b->ran = true;
+    if (L.nitems == 0) return launch_tc_grids(b, L, ins, outs, steps, st);
     size_t smem = 0;
     const size_t es = b->dtype == STENCIL_F64 ? 8 : 4;
     for (auto &g : b->grids) {
+        if (!g.on_cu()) continue;
         const int R = g.plan.pat.r, t = g.plan.t;
         smem = std::max(smem, (size_t)(g.plan.tile[1] + 2 * t * R) * (g.plan.tile[2] + 2 * t * R) * es * 2);
     }
@@ -361,10 +388,9 @@ stencil_status launch_batch(stencil_batch *b, const Layout &L, cudaStream_t st, 
         bt::batch_sweeps<float><<<grid, bt::kThreads, smem, st>>>(gd, items, L.nitems, (const float *)(ws + L.w_off),
                                                                   done, ctl, b->wait_cycles, b->block_sweep);
     if (count) note_launch();
-    b->ctl_off = L.ctl_off;
-    b->ran = true;
     e = cudaGetLastError();
-    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "batch_sweeps launch");
+    if (e != cudaSuccess) return cuda_fail(e, "batch_sweeps launch");
+    return launch_tc_grids(b, L, ins, outs, steps, st);
 }
 
 // Host tables for one run: grid descriptors with this run's pointers, the
@@ -388,7 +414,7 @@ stencil_status upload_tables(stencil_batch *b, const Layout &L, const void *cons
         g.ex = p.ext[2];
         g.kind = p.pat.shape * 4 + p.pat.r;
         g.t = p.t;
-        g.nsweeps = sweeps_of(p, steps);
+        g.nsweeps = b->grids[i].on_cu() ? sweeps_of(p, steps) : 0;  // tensor-core grids have no items
         g.rem = (int)(steps % p.t);
         g.by = p.tile[1];
         g.bx = p.tile[2];
@@ -428,6 +454,24 @@ stencil_status check_run_args(stencil_batch *b, const void *const *ins, void *co
     if (!b->ws || b->ws_bytes < L->total)
         return fail(STENCIL_ERR_OOM, "stencil_batch_run: workspace smaller than stencil_batch_workspace_bytes");
     return STENCIL_OK;
+}
+
+// One staging + one work buffer per work item: the CUDA-core default tile,
+// halved until the grown tile pair fits in ~100 KB.
+void batch_tile(Plan *p)
+{
+    int tile[3];
+    cu_default_tile(*p, p->t, tile);
+    for (;;) {
+        const size_t bytes =
+            (size_t)(tile[1] + 2 * p->t * p->pat.r) * (tile[2] + 2 * p->t * p->pat.r) * p->elem_bytes() * 2;
+        if (bytes <= 100 * 1024 || (tile[1] <= 16 && tile[2] <= 16)) break;
+        if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
+    }
+    for (int k = 0; k < 3; k++) p->tile[k] = tile[k];
+    p->info.tile[0] = tile[0];
+    p->info.tile[1] = tile[1];
+    p->info.tile[2] = tile[2];
 }
 
 void drop_graph(BatchCache &c)
@@ -477,16 +521,7 @@ stencil_status stencil_batch_create(stencil_batch **batch, int n, const stencil_
         BatchGridHost g;
         g.plan = p->p;
         stencil_plan_destroy(p);
-        // one staging + one work buffer per item: keep the tile within ~100 KB
-        int tile[3];
-        cu_default_tile(g.plan, g.plan.t, tile);
-        for (;;) {
-            size_t bytes = (size_t)(tile[1] + 2 * g.plan.t * d.r) * (tile[2] + 2 * g.plan.t * d.r) *
-                           g.plan.elem_bytes() * 2;
-            if (bytes <= 100 * 1024 || (tile[1] <= 16 && tile[2] <= 16)) break;
-            if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
-        }
-        for (int k = 0; k < 3; k++) g.plan.tile[k] = tile[k];
+        batch_tile(&g.plan);
         b->grids.push_back(std::move(g));
     }
     *batch = b;
@@ -536,7 +571,7 @@ stencil_status stencil_batch_run(stencil_batch *batch, const void *const *ins, v
     drop_graph(batch->cache);  // the tables are about to change
     s = upload_tables(batch, L, ins, outs, steps, st);
     if (s != STENCIL_OK) return s;
-    return launch_batch(batch, L, st, true);
+    return launch_batch(batch, L, ins, outs, steps, st, true);
 }
 
 stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
@@ -558,7 +593,7 @@ stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *
         if (s != STENCIL_OK) return s;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run_graph: begin capture");
-        s = launch_batch(batch, L, st, false);  // counted at each replay
+        s = launch_batch(batch, L, ins, outs, steps, st, false);  // counted at each replay
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         if (s != STENCIL_OK) {
@@ -572,6 +607,17 @@ stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *
             return cuda_fail(e, "stencil_batch_run_graph: instantiate");
         }
         c.graph = g;
+        size_t nn = 0;
+        c.kernel_nodes = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (auto nd : nodes) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                        c.kernel_nodes++;
+                }
+        }
         c.ins.assign(ins, ins + n);
         c.outs.assign(outs, outs + n);
         c.steps = steps;
@@ -580,7 +626,7 @@ stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *
     }
     cudaError_t e = cudaGraphLaunch(c.exec, st);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run_graph: launch");
-    note_launch();
+    note_launch(c.kernel_nodes);
     return STENCIL_OK;
 }
 
@@ -600,6 +646,43 @@ stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t strea
 stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, const char *value)
 {
     if (!batch || !key || !value) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_option: null argument");
+    const std::string ks(key), vs(value);
+    if (ks == "precision") {
+        int pr;
+        if (vs == "native") pr = STENCIL_PREC_NATIVE;
+        else if (vs == "tf32") pr = STENCIL_PREC_TF32;
+        else if (vs == "tf32x3") pr = STENCIL_PREC_TF32X3;
+        else if (vs == "bf16x3") pr = STENCIL_PREC_BF16X3;
+        else if (vs == "any") pr = STENCIL_PREC_ANY;
+        else return fail(STENCIL_ERR_INVALID_ARG, "batch precision must be native|tf32|tf32x3|bf16x3|any");
+        if (batch->dtype == STENCIL_F64 && pr != STENCIL_PREC_NATIVE)
+            return fail(STENCIL_ERR_UNSUPPORTED, "batch precision: FP64 grids compute natively");
+        batch->precision = pr;
+        return STENCIL_OK;
+    }
+    if (ks == "path") {
+        // every grid on this path (its model-chosen form and t)
+        int path;
+        if (vs == "auto") path = STENCIL_PATH_AUTO;
+        else if (vs == "cuda_core") path = STENCIL_PATH_CUDA_CORE;
+        else if (vs == "tensor_core") path = STENCIL_PATH_TENSOR_CORE;
+        else if (vs == "sparse_tensor_core") path = STENCIL_PATH_SPARSE_TENSOR_CORE;
+        else return fail(STENCIL_ERR_INVALID_ARG, "batch path must be auto|cuda_core|tensor_core|sparse_tensor_core");
+        std::vector<Plan> plans;
+        for (auto &g : batch->grids) {
+            Plan q = g.plan;
+            q.req_path = path;
+            q.req_precision = path == STENCIL_PATH_CUDA_CORE ? STENCIL_PREC_NATIVE : batch->precision;
+            q.req_tile[0] = q.req_tile[1] = q.req_tile[2] = 0;
+            stencil_status s = dispatch(&q);
+            if (s != STENCIL_OK) return s;
+            if (q.path == STENCIL_PATH_CUDA_CORE) batch_tile(&q);
+            plans.push_back(q);
+        }
+        for (size_t i = 0; i < plans.size(); i++) batch->grids[i].plan = plans[i];
+        drop_graph(batch->cache);
+        return STENCIL_OK;
+    }
     char *end = nullptr;
     const long long v = std::strtoll(value, &end, 10);
     if (!*value || *end) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_option: value must be an integer");
@@ -615,6 +698,212 @@ stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, c
     }
     drop_graph(batch->cache);
     return STENCIL_OK;
+}
+
+// Autotuner of the batched form.  Grids are grouped into shape classes
+// (stencil shape and radius, and size class c: interior points in
+// [4^(6+c), 4^(7+c)), i.e. sides around 64 * 2^c).  For each class the
+// candidates -- CUDA-core work items with t = 1..4 and tiles from 16 x 64 to
+// 128 x 128, and, where the batch precision allows and the grids are large,
+// the dense and sparse tensor-core paths with t = 1..4 -- are ranked by the
+// model (the dispatcher's prediction for the class's first grid); the
+// model's best kTunePerPath of each path plus the current choice are
+// measured on a batch made of the class's grids alone (CUDA events on
+// `stream`, after one untimed run), and the fastest becomes the choice of
+// every grid of the class.
+static const int kTuneTiles[][2] = {{16, 64}, {32, 64}, {32, 128}, {64, 64}, {64, 128}, {128, 128}};
+constexpr int kTunePerPath = 4;
+
+static int size_class(const Plan &p)
+{
+    const double pts = (double)p.dims[1] * (double)p.dims[2];
+    int c = (int)std::floor(std::log2(std::max(pts, 1.0)) / 2.0) - 6;
+    return std::min(6, std::max(0, c));
+}
+
+stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
+                                      int reps, stencil_stream_t stream, stencil_batch_tune_result *results,
+                                      int max_results, int *n_results)
+{
+    if (n_results) *n_results = 0;
+    if (steps < 1 || reps < 1) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_autotune: steps and reps >= 1");
+    Layout L0;
+    stencil_status s = check_run_args(batch, ins, outs, steps, &L0);
+    if (s != STENCIL_OK) return s;
+    drop_graph(batch->cache);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = batch->dtype == STENCIL_F64 ? 8 : 4;
+    std::map<long, std::vector<int>> classes;
+    for (size_t i = 0; i < batch->grids.size(); i++) {
+        const Plan &p = batch->grids[i].plan;
+        classes[(long)p.pat.shape * 10000 + p.pat.r * 100 + size_class(p)].push_back((int)i);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(STENCIL_ERR_CUDA, "stencil_batch_autotune: cudaEventCreate");
+    }
+    struct Cand {
+        int path, prec, t, ty, tx;
+        double model, measured;
+    };
+    int nres = 0, cls = 0;
+    for (auto &kv : classes) {
+        const std::vector<int> &members = kv.second;
+        const Plan &base = batch->grids[members[0]].plan;
+        const int r = base.pat.r, sc = size_class(base);
+        int64_t maxy = 0, maxx = 0;
+        double pts = 0;
+        for (int i : members) {
+            maxy = std::max(maxy, batch->grids[i].plan.dims[1]);
+            maxx = std::max(maxx, batch->grids[i].plan.dims[2]);
+            pts += (double)batch->grids[i].plan.dims[1] * (double)batch->grids[i].plan.dims[2];
+        }
+        // configure plan q for a candidate; false if no kernel takes it
+        auto configure = [&](Plan *q, const Cand &c) {
+            q->req_path = c.path;
+            q->req_precision = c.prec;
+            q->req_t = c.t;
+            q->req_tile[0] = q->req_tile[1] = q->req_tile[2] = 0;
+            if (c.path == STENCIL_PATH_CUDA_CORE) {
+                q->req_tile[0] = 1;
+                q->req_tile[1] = c.ty;
+                q->req_tile[2] = c.tx;
+            }
+            return dispatch(q) == STENCIL_OK;
+        };
+        std::vector<Cand> cands;
+        for (int t = 1; t <= 4; t++)
+            for (auto &tl : kTuneTiles) {
+                const int ty = tl[0], tx = tl[1];
+                if ((size_t)(ty + 2 * t * r) * (tx + 2 * t * r) * es * 2 > 100 * 1024) continue;
+                if (ty > 2 * std::max<int64_t>(16, maxy) || tx > 2 * std::max<int64_t>(64, maxx)) continue;
+                Cand c{STENCIL_PATH_CUDA_CORE, STENCIL_PREC_NATIVE, t, ty, tx, 0, 0};
+                Plan q = base;
+                if (configure(&q, c)) {
+                    c.model = q.info.predicted_gstencils;
+                    cands.push_back(c);
+                }
+            }
+        const bool tc_ok = batch->dtype == STENCIL_F64 || batch->precision != STENCIL_PREC_NATIVE;
+        if (tc_ok && sc >= 3) {
+            std::vector<int> precs;
+            if (batch->dtype == STENCIL_F64) precs = {STENCIL_PREC_NATIVE};
+            else if (batch->precision == STENCIL_PREC_ANY) precs = {STENCIL_PREC_TF32, STENCIL_PREC_TF32X3, STENCIL_PREC_BF16X3};
+            else precs = {batch->precision};
+            for (int path : {STENCIL_PATH_TENSOR_CORE, STENCIL_PATH_SPARSE_TENSOR_CORE})
+                for (int pr : precs)
+                    for (int t = 1; t <= 4 && t * r <= 12; t++) {
+                        Cand c{path, pr, t, 0, 0, 0, 0};
+                        Plan q = base;
+                        if (configure(&q, c)) {
+                            c.model = q.info.predicted_gstencils;
+                            c.ty = q.tile[1];
+                            c.tx = q.tile[2];
+                            cands.push_back(c);
+                        }
+                    }
+        }
+        std::stable_sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b) { return a.model > b.model; });
+        {
+            // the model's best kTunePerPath of each path
+            std::vector<Cand> keep;
+            int taken[4] = {0, 0, 0, 0};
+            for (auto &c : cands)
+                if (taken[c.path]++ < kTunePerPath) keep.push_back(c);
+            cands.swap(keep);
+        }
+        // the current choice is always among the measured
+        {
+            Cand cur{base.path, base.precision, base.t, base.tile[1], base.tile[2], base.info.predicted_gstencils, 0};
+            bool have = false;
+            for (auto &c : cands)
+                have |= c.path == cur.path && c.prec == cur.prec && c.t == cur.t &&
+                        (c.path != STENCIL_PATH_CUDA_CORE || (c.ty == cur.ty && c.tx == cur.tx));
+            if (!have) cands.push_back(cur);
+        }
+        int best = -1;
+        std::vector<Plan> best_plans;
+        for (size_t ci = 0; ci < cands.size(); ci++) {
+            Cand &c = cands[ci];
+            stencil_batch sub;
+            sub.dtype = batch->dtype;
+            sub.ws = batch->ws;
+            sub.ws_bytes = batch->ws_bytes;
+            sub.wait_cycles = batch->wait_cycles;
+            std::vector<const void *> sin;
+            std::vector<void *> sout;
+            bool ok = true;
+            for (int i : members) {
+                BatchGridHost g = batch->grids[i];
+                ok = ok && configure(&g.plan, c);
+                sub.grids.push_back(g);
+                sin.push_back(ins[i]);
+                sout.push_back(outs[i]);
+            }
+            if (!ok) continue;
+            const Layout Ls = layout_of(sub, steps);
+            if (Ls.total > sub.ws_bytes) continue;  // does not fit the caller's workspace
+            s = upload_tables(&sub, Ls, sin.data(), sout.data(), steps, st);
+            if (s == STENCIL_OK) s = launch_batch(&sub, Ls, sin.data(), sout.data(), steps, st, true);
+            if (s == STENCIL_OK && cudaEventRecord(e0, st) != cudaSuccess) s = fail(STENCIL_ERR_CUDA, "event");
+            for (int k = 0; k < reps && s == STENCIL_OK; k++)
+                s = launch_batch(&sub, Ls, sin.data(), sout.data(), steps, st, true);
+            if (s == STENCIL_OK && cudaEventRecord(e1, st) != cudaSuccess) s = fail(STENCIL_ERR_CUDA, "event");
+            if (s != STENCIL_OK) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(e, "stencil_batch_autotune: timing");
+                break;
+            }
+            bt::Ctl ctl{};
+            e = cudaMemcpy(&ctl, (char *)sub.ws + Ls.ctl_off, sizeof(ctl), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                s = cuda_fail(e, "stencil_batch_autotune: control word");
+                break;
+            }
+            if (ctl.abort) {
+                s = fail(STENCIL_ERR_TIMEOUT, "stencil_batch_autotune: a dependency wait ran out");
+                break;
+            }
+            c.measured = pts * (double)steps * reps / (ms * 1e-3) / 1e9;
+            if (best < 0 || c.measured > cands[best].measured) {
+                best = (int)ci;
+                best_plans.clear();
+                for (auto &g : sub.grids) best_plans.push_back(g.plan);
+            }
+        }
+        if (s != STENCIL_OK) break;
+        if (best >= 0)
+            for (size_t k = 0; k < members.size(); k++) batch->grids[members[k]].plan = best_plans[k];
+        for (size_t ci = 0; ci < cands.size(); ci++) {
+            if (results && nres < max_results) {
+                stencil_batch_tune_result &o = results[nres];
+                o.cls = cls;
+                o.shape = base.pat.shape;
+                o.r = r;
+                o.size_class = sc;
+                o.ngrids = (int)members.size();
+                o.path = cands[ci].path;
+                o.precision = cands[ci].prec;
+                o.t = cands[ci].t;
+                o.tile_y = cands[ci].ty;
+                o.tile_x = cands[ci].tx;
+                o.model_gstencils = cands[ci].model;
+                o.measured_gstencils = cands[ci].measured;
+                o.chosen = (int)ci == best;
+            }
+            nres++;
+        }
+        cls++;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    batch->ran = false;
+    if (n_results) *n_results = nres;
+    return s;
 }
 
 void stencil_batch_destroy(stencil_batch *batch)

@@ -31,6 +31,11 @@ stencil_status read_device_error(int *flag);
 // to `out2`.
 stencil_status launch_halo_copy(const Plan &p, const void *in, void *out, void *out2, cudaStream_t st);
 
+// The whole run of a plan (halo copy, ceil(steps/t) fused sweeps on the
+// plan's path, ping-pong through ws) on `st`; what stencil_run enqueues.
+stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, size_t ws_bytes, int64_t steps,
+                          cudaStream_t st);
+
 // Raise the dynamic shared-memory limit of `func` to `bytes` once.
 stencil_status ensure_smem(const void *func, size_t bytes, int *cached);
 

@@ -65,7 +65,7 @@ stencil_status launch_halo_copy(const Plan &p, const void *in, void *out, void *
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "halo_copy launch");
 }
 
-static stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, size_t ws_bytes, int64_t steps,
+stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, size_t ws_bytes, int64_t steps,
                                  cudaStream_t st)
 {
     if (steps == 0) {

@@ -225,3 +225,42 @@ def test_batch_workspace_and_no_launch_without_it(lib):
         assert B.stencil_launch_count() == n0
     finally:
         B.stencil_batch_destroy(h)
+
+
+def test_batch_precision_and_path_options(lib):
+    grids = [("box", 2, 300, 310, _w("box", 2, 2)), ("star", 1, 40, 70, _w("star", 2, 1))]
+    h = B.stencil_batch_create(grids, "f32", 0)
+    try:
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_batch_set_option(h, "precision", "fp8")
+        assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        with pytest.raises(B.StencilError) as e:  # FP32 native has no tensor-core form
+            B.stencil_batch_set_option(h, "path", "tensor_core")
+        assert e.value.status == B.STENCIL_ERR_UNSUPPORTED
+        assert B.stencil_batch_info(h, 0)["path"] == B.PATH_CUDA_CORE  # unchanged after the refusal
+        B.stencil_batch_set_option(h, "precision", "tf32x3")
+        B.stencil_batch_set_option(h, "path", "tensor_core")
+        for i in range(2):
+            info = B.stencil_batch_info(h, i)
+            assert info["path"] == B.PATH_TENSOR_CORE and info["precision"] == B.PREC_TF32X3
+        B.stencil_batch_set_option(h, "path", "cuda_core")
+        assert B.stencil_batch_info(h, 1)["path"] == B.PATH_CUDA_CORE
+        n0 = B.stencil_launch_count()
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_batch_autotune(h, [4096, 8192], [1 << 20, 1 << 21], 0, stream=0)
+        assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        with pytest.raises(B.StencilError) as e:  # no workspace
+            B.stencil_batch_autotune(h, [4096, 8192], [1 << 20, 1 << 21], 5, stream=0)
+        assert e.value.status == B.STENCIL_ERR_OOM
+        assert B.stencil_launch_count() == n0
+    finally:
+        B.stencil_batch_destroy(h)
+    h64 = B.stencil_batch_create(grids, "f64", 0)
+    try:
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_batch_set_option(h64, "precision", "tf32")
+        assert e.value.status == B.STENCIL_ERR_UNSUPPORTED
+        B.stencil_batch_set_option(h64, "path", "tensor_core")  # FP64 MMA
+        assert B.stencil_batch_info(h64, 0)["path"] == B.PATH_TENSOR_CORE
+    finally:
+        B.stencil_batch_destroy(h64)
