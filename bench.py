@@ -243,10 +243,14 @@ def _time_runs(fn, stream, reps=3, warm=1):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def mixed_precision_leg(B, inputs, stream, steps=100):
-    """Box-2D2R FP32 16384^2 (sine-mode field): plain FP32 on CUDA cores at the
-    model's t against the tensor-core TF32, TF32x3 and BF16x3 forms at each
-    t = 1..4 (point-updates/s; errors are checked in the GPU tests)."""
+def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
+    """Box-2D2R FP32 16384^2 (sine-mode field): plain FP32 on CUDA cores
+    against the tensor-core TF32, TF32x3 and BF16x3 forms and the sparse TF32
+    form at each t = 1..4 (point-updates/s over `steps`-step runs), then, for
+    plain FP32 and each form at its fastest t, the normwise relative error
+    every `every` steps up to `horizon` steps against the FP64 CUDA-core path
+    run on the GPU from the same field (the reference the GPU tests hold
+    within 1e-12 of the FP64 oracle)."""
     import numpy as np
     import torch
     dims = (16384, 16384)
@@ -256,7 +260,8 @@ def mixed_precision_leg(B, inputs, stream, steps=100):
     pts = dims[0] * dims[1]
     rows = []
     cands = [("cuda_core", "native", t) for t in (1, 2, 3, 4)] + \
-            [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3") for t in (1, 2, 3, 4)]
+            [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3") for t in (1, 2, 3, 4)] + \
+            [("sparse_tensor_core", "tf32", t) for t in (1, 2, 3, 4)]
     for path, prec, t in cands:
         plan = B.Plan("box", 2, 2, w, "f32", dims, t)
         if prec != "native":
@@ -269,12 +274,52 @@ def mixed_precision_leg(B, inputs, stream, steps=100):
                      "model_gstencils": info["predicted_gstencils"], "alpha": info["alpha"],
                      "sparsity": info["sparsity"], "beta": info["beta"]})
         plan.close()
-    del x, y
-    torch.cuda.empty_cache()
     plain = max(r["gstencils"] for r in rows if r["path"] == "cuda_core")
     best = max(rows, key=lambda r: r["gstencils"])
-    return {"workload": f"Box-2D2R F32 16384x16384, sine-mode field, {steps} steps per run",
-            "plain_fp32_cuda_core_gstencils": plain, "best": best, "rows": rows}
+
+    # error growth: FP64 reference states every `every` steps (kept on the GPU)
+    ref_plan = B.Plan("box", 2, 2, w, "f64", dims, 0)
+    ref_plan.set_option("path", "cuda_core")
+    a64 = x.double()
+    b64 = torch.empty_like(a64)
+    ref_plan.ensure_workspace(a64.device)
+    refs = []
+    for _ in range(horizon // every):
+        ref_plan.run(a64, b64, every)
+        refs.append(b64[2:-2, 2:-2].clone())
+        a64, b64 = b64, a64
+    ref_plan.close()
+    del a64, b64
+    errors = []
+    fastest = {}
+    for r in rows:
+        k = (r["path"], r["precision"])
+        if k not in fastest or r["gstencils"] > fastest[k]["gstencils"]:
+            fastest[k] = r
+    for (path, prec), r in fastest.items():
+        plan = B.Plan("box", 2, 2, w, "f32", dims, r["t"])
+        if prec != "native":
+            plan.set_option("precision", prec)
+        plan.set_option("path", path)
+        plan.ensure_workspace(x.device)
+        a, b = x.clone(), torch.empty_like(x)
+        curve = []
+        for k, ref in enumerate(refs):
+            plan.run(a, b, every)
+            d = (b[2:-2, 2:-2].double() - ref).abs().max() / ref.abs().max()
+            curve.append({"steps": (k + 1) * every, "rel_linf": float(d)})
+            a, b = b, a
+        plan.close()
+        del a, b
+        errors.append({"path": path, "precision": prec, "t": r["t"], "gstencils": r["gstencils"],
+                       "error_vs_fp64": curve,
+                       "meets_2e-6_at": [c["steps"] for c in curve if c["rel_linf"] <= 2e-6]})
+    del refs, x, y
+    torch.cuda.empty_cache()
+    return {"workload": f"Box-2D2R F32 16384x16384, sine-mode field, {steps} steps per timed run; "
+                        f"error every {every} steps to {horizon}",
+            "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests)",
+            "plain_fp32_cuda_core_gstencils": plain, "best": best, "rows": rows, "errors": errors}
 
 
 def batched_leg(B, inputs, stream, steps=20):
@@ -297,8 +342,24 @@ def batched_leg(B, inputs, stream, steps=20):
     batch = B.Batch(probs, "f32", 0)
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
+        # the model's choice per grid, then the autotuned choice per shape class
+        sec_model = _time_runs(lambda: batch.run(ins, outs, steps, stream=side, graph=True), side)
+        t0 = time.perf_counter()
+        tune = batch.autotune(ins, outs, steps, reps=1, stream=side)
+        tune_s = time.perf_counter() - t0
+        n0 = B.stencil_launch_count()
+        batch.run(ins, outs, steps, stream=side, graph=True)  # capture + replay
+        side.synchronize()
+        n1 = B.stencil_launch_count()
         sec_graph = _time_runs(lambda: batch.run(ins, outs, steps, stream=side, graph=True), side)
+        n2 = B.stencil_launch_count()
         sec_batch = _time_runs(lambda: batch.run(ins, outs, steps, stream=side, graph=False), side)
+    graph_launches = (n2 - n1) // 4  # per replay (_time_runs: 1 warm + 3 timed)
+    chosen = [q for q in tune if q["chosen"]]
+    picks = {}
+    for q in chosen:
+        key = f"{q['path']}:t{q['t']}:{q['tile_y']}x{q['tile_x']}"
+        picks[key] = picks.get(key, 0) + q["ngrids"]
     plans = [B.Plan(s, 2, r, w, "f32", (ny, nx), 0) for (s, r, ny, nx, w) in probs]
     for p in plans:
         p.set_option("path", "cuda_core")
@@ -321,8 +382,11 @@ def batched_leg(B, inputs, stream, steps=20):
                         f"{steps} steps, {pts} interior points",
             "persistent_graph_gstencils": pts * steps / sec_graph / 1e9,
             "persistent_gstencils": pts * steps / sec_batch / 1e9,
+            "persistent_graph_model_choice_gstencils": pts * steps / sec_model / 1e9,
             "per_grid_loop_gstencils": pts * steps / sec_loop / 1e9,
-            "per_grid_loop_launches": loop_launches, "persistent_launches": 1}
+            "per_grid_loop_launches": loop_launches, "persistent_graph_kernel_launches": graph_launches,
+            "autotune": {"classes": len(chosen), "candidates_measured": sum(1 for q in tune if q["measured_gstencils"] > 0),
+                         "seconds": tune_s, "grids_per_choice": picks}}
 
 
 def main():
@@ -429,7 +493,7 @@ def main():
     avg_launch_s = ms / 1e3 / sweep_launches
     K = info["K"]
     D = 8 if cfg["dtype"] == "f64" else 4
-    kernel = {1: "cu2d_sweep" if cfg["d"] == 2 else "cu3d_sweep"}.get(info["path"], "tc_sweep")
+    kernel = {1: "cu2d_sweep" if cfg["d"] == 2 else "cu3d_sweep", 3: "sptc2d_sweep"}.get(info["path"], "tc_sweep")
     kernel_key = f"{kernel}:{args.config}:{info['path_name']}:t{t}"
     traffic = traffic_record(kernel_key)
     if info["memory_bound"]:
