@@ -79,6 +79,54 @@ constexpr int kSpTY = 128, kSpTX = 64;
 //   selectors (selector 0: lanes with q < 2): lane 4g + h, nibble i ->
 //   (row g, pair 4h + i), nibble 4 + i -> (row g + 8, pair 4h + i);
 //   0x4 keeps the first member of the pair, 0xE the second.
+// One pass over NL consecutive lines (a_lo .. a_lo+NL-1) of the composite:
+// their compressed A fragments are held in registers; for each input row
+// offset rho the B fragments (one 16-byte load per instruction) are loaded
+// once, one row ahead, and fed to every (accumulator y0, line a) with
+// y0 + a = rho.
+template <int NS, int NL>
+__device__ __forceinline__ void sp_pass(float (&acc)[8][4], const float *Tw, int a_lo, int RP, const int (&boff0)[NS],
+                                        const int (&boff1)[NS], int g, const float4 *Af, const uint32_t *Em,
+                                        const unsigned char *mask, int lane)
+{
+    float4 A[NL][NS];
+    uint32_t E[NL][NS];
+    unsigned mk[NL];
+#pragma unroll
+    for (int al = 0; al < NL; al++) {
+        mk[al] = mask[a_lo + al];
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            const int idx = ((a_lo + al) * NS + s) * 32 + lane;
+            A[al][s] = Af[idx];
+            E[al][s] = Em[idx];
+        }
+    }
+    auto loadB = [&](int rho, float4 (&Bv)[NS]) {
+        const int swz = ((rho >> 3) ^ g) & 1;  // bit 3 of the staged row rho + 8 g
+        const float *srow = Tw + (size_t)rho * RP;
+#pragma unroll
+        for (int s = 0; s < NS; s++) Bv[s] = *reinterpret_cast<const float4 *>(srow + (swz ? boff1[s] : boff0[s]));
+    };
+    float4 Bc[NS], Bn[NS];
+    loadB(a_lo, Bc);
+#pragma unroll
+    for (int rr = 0; rr < NL + 7; rr++) {
+        if (rr + 1 < NL + 7) loadB(a_lo + rr + 1, Bn);
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+#pragma unroll
+            for (int y0 = 0; y0 < 8; y0++) {
+                const int al = rr - y0;
+                if (al < 0 || al >= NL) continue;
+                if ((mk[al] >> s) & 1u) mma_sp(acc[y0], A[al][s], Bc[s], E[al][s]);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NS; s++) Bc[s] = Bn[s];
+    }
+}
+
 template <int NS, int LC>
 __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__ in, float *__restrict__ out,
                                                        const __grid_constant__ SpParams p, int ntiles, int ntx)
@@ -182,41 +230,15 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
         for (int y = 0; y < 8; y++) acc[y][0] = acc[y][1] = acc[y][2] = acc[y][3] = 0.0f;
 
         const float *Tw = T + (size_t)(64 * wb + 8 * g) * RP;
-        for (int a_lo = 0; a_lo < lines; a_lo += LC) {
-            const int nl = min(LC, lines - a_lo);
-            float4 A[LC][NS];
-            uint32_t E[LC][NS];
-            unsigned mk[LC];
-#pragma unroll
-            for (int al = 0; al < LC; al++) {
-                mk[al] = al < nl ? p.mask[a_lo + al] : 0u;
-#pragma unroll
-                for (int s = 0; s < NS; s++) {
-                    const int idx = ((a_lo + (al < nl ? al : 0)) * NS + s) * 32 + lane;
-                    A[al][s] = Af[idx];
-                    E[al][s] = Em[idx];
-                }
-            }
-#pragma unroll
-            for (int rr = 0; rr < LC + 7; rr++) {
-                if (rr >= nl + 7) break;
-                const int rho = a_lo + rr;  // input row offset of the band (+ 8 g)
-                const int swz = ((rho >> 3) ^ g) & 1;
-                const float *srow = Tw + (size_t)rho * RP;
-                float4 Bv[NS];
-#pragma unroll
-                for (int s = 0; s < NS; s++)
-                    Bv[s] = *reinterpret_cast<const float4 *>(srow + (swz ? boff1[s] : boff0[s]));
-#pragma unroll
-                for (int s = 0; s < NS; s++) {
-#pragma unroll
-                    for (int y0 = 0; y0 < 8; y0++) {
-                        const int al = rr - y0;
-                        if (al < 0 || al >= LC) continue;
-                        if ((mk[al] >> s) & 1u) mma_sp(acc[y0], A[al][s], Bv[s], E[al][s]);
-                    }
-                }
-            }
+        int a_lo = 0;
+        for (; a_lo + LC <= lines; a_lo += LC)
+            sp_pass<NS, LC>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane);
+        switch (lines - a_lo) {  // the last, partial pass: no predicated-off MMAs
+        case 1: sp_pass<NS, 1>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 2: if constexpr (LC > 2) sp_pass<NS, 2>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 3: if constexpr (LC > 3) sp_pass<NS, 3>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 4: if constexpr (LC > 4) sp_pass<NS, 4>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        default: break;
         }
 
         // epilogue: d0 (col g, row slot 2q), d1 (g, 2q+1), d2 (g+8, 2q), d3 (g+8, 2q+1);
@@ -315,7 +337,7 @@ stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t
     switch (L.ns) {
     case 2: s = launch_ns<2, 5>(sp, in, out, p.dims[1], p.dims[2], st); break;
     case 3: s = launch_ns<3, 4>(sp, in, out, p.dims[1], p.dims[2], st); break;
-    case 4: s = launch_ns<4, 3>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 4: s = launch_ns<4, 2>(sp, in, out, p.dims[1], p.dims[2], st); break;
     default: return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path: layout");
     }
     if (s != STENCIL_OK || t == 1) return s;
