@@ -241,6 +241,149 @@ __device__ __forceinline__ void f32_substep(const float *__restrict__ src, float
     }
 }
 
+// Row pitch of a staged tile row of width W and the elements of one staging
+// buffer of H rows: FP32 rows are padded to 16-byte multiples (the 4-column
+// sub-step reads them with 16-byte loads) and each buffer has 8 elements of
+// slack at its end (the last window of the last row reads past column W).
+template <typename T>
+__host__ __device__ constexpr int row_pitch(int W)
+{
+    return sizeof(T) == 4 ? (W + 3) & ~3 : W;
+}
+template <typename T>
+__host__ __device__ constexpr size_t buf_elems(int H, int W)
+{
+    return (size_t)H * row_pitch<T>(W) + (sizeof(T) == 4 ? 8 : 0);
+}
+
+// FP32 sub-step, 4-column register-rotation form.  A work item is a quad of
+// adjacent columns (x .. x+3) and a strip of S output rows.  The thread walks
+// down the strip's input rows once; each row window (columns x-R-D ..,
+// D = (lo-R) mod 4 so the window starts on a 16-byte boundary) is read with
+// 16-byte shared loads and added to the 2R+1 output rows it touches, whose
+// partial sums rotate through 2R+1 register slots.  The first 2R+1 input rows
+// are peeled so that no FMA goes into an output above the strip; the row loop
+// is unrolled by 2R+1, so every slot and weight index is a compile-time
+// constant.  Output row jj is complete after input row jj + 2R and is stored
+// (as two 8-byte or four 4-byte stores, by alignment) from its slot.  P is
+// the row pitch of src and dst (a multiple of 4).
+template <int SHAPE, int R, int D, typename WT>
+__device__ __forceinline__ void f32_substep4(const float *__restrict__ src, float *__restrict__ dst,
+                                             float *__restrict__ out, const WT &wt, int P, int lo, int hiY, int hiX,
+                                             int64_t Y0, int64_t X0, int64_t Ey, int64_t Ex, bool last,
+                                             bool all_interior, int band)
+{
+    constexpr int NS = 2 * R + 1;          // rotating slots
+    constexpr int NV = 2 * R + 4 + D;      // window values per row
+    constexpr int NL = (NV + 3) / 4;       // 16-byte loads per row
+    const int cw = hiX - lo, ch = hiY - lo;
+    const int nquads = (cw + 3) / 4;
+    // strips of >= 8 rows, enough of them to give every thread work
+    const int nstrips = max(1, min((ch + 7) / 8, (int)((blockDim.x + nquads - 1) / nquads)));
+    const int S = (ch + nstrips - 1) / nstrips;
+    const int64_t ny = Ey - 2 * R, nx = Ex - 2 * R;
+    const bool fast = all_interior && band == 0;
+
+    for (int item = threadIdx.x; item < nstrips * nquads; item += blockDim.x) {
+        const int sy = item / nquads, qx = item - sy * nquads;
+        const int y0 = lo + sy * S;
+        const int yend = min(y0 + S, hiY);  // outputs y0 .. yend-1
+        if (y0 >= yend) continue;
+        const int x = lo + 4 * qx;
+        const int nval = min(4, hiX - x);
+        const int nrows = (yend - y0) + 2 * R;  // input rows y0-R .. yend-1+R
+        const float *col = src + x - R - D;
+        // output store of row y (4 values), by alignment and boundary
+        auto store = [&](int y, const float (&a)[4]) {
+            if (fast && nval == 4) {
+                float *o = last ? out + (Y0 + y) * Ex + (X0 + x) : dst + y * P + x;
+                const uintptr_t al = reinterpret_cast<uintptr_t>(o) & 15;
+                if (al == 0) {
+                    *reinterpret_cast<float4 *>(o) = make_float4(a[0], a[1], a[2], a[3]);
+                } else if ((al & 7) == 0) {
+                    reinterpret_cast<float2 *>(o)[0] = make_float2(a[0], a[1]);
+                    reinterpret_cast<float2 *>(o)[1] = make_float2(a[2], a[3]);
+                } else {
+                    o[0] = a[0];
+                    o[1] = a[1];
+                    o[2] = a[2];
+                    o[3] = a[3];
+                }
+                return;
+            }
+            const int64_t gy = Y0 + y;
+            const bool rowint = gy >= R && gy < Ey - R;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                if (h >= nval) break;
+                const int64_t gx = X0 + x + h;
+                const bool interior = rowint && gx >= R && gx < Ex - R;
+                if (last) {
+                    bool keep = interior;
+                    if (band > 0) {
+                        const int64_t iy = gy - R, ix = gx - R;
+                        keep = keep && (iy < band || ix < band || ny - 1 - iy < band || nx - 1 - ix < band);
+                    }
+                    if (keep) out[gy * Ex + gx] = a[h];
+                } else {
+                    dst[y * P + x + h] = interior ? a[h] : src[y * P + x + h];
+                }
+            }
+        };
+        float acc[NS][4];
+#pragma unroll
+        for (int m = 0; m < NS; ++m) acc[m][0] = acc[m][1] = acc[m][2] = acc[m][3] = 0.0f;
+        // one input row (relative row qq, unrolled position u) into the slots
+        // of outputs qq - e for e in [0, e_hi]
+        auto row = [&](int qq, int u, int e_hi) {
+            const float4 *rp = reinterpret_cast<const float4 *>(col + (y0 - R + qq) * P);
+            float v[4 * NL];
+#pragma unroll
+            for (int c = 0; c < NL; ++c) {
+                const float4 t4 = rp[c];
+                v[4 * c] = t4.x;
+                v[4 * c + 1] = t4.y;
+                v[4 * c + 2] = t4.z;
+                v[4 * c + 3] = t4.w;
+            }
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+                if (e > e_hi) continue;
+                const int slot = ((u - e) % NS + NS) % NS;
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    const int k = tap_index<SHAPE, 2, R>(0, e - R, ox);
+                    if (k >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[slot][c] = fmaf(wt.w[k], v[D + R + ox + c], acc[slot][c]);
+                    }
+                }
+            }
+        };
+        // head: input row u (u <= 2R) feeds only outputs u - e >= 0
+#pragma unroll
+        for (int u = 0; u < NS; ++u)
+            if (u < nrows) row(u, u, u);
+        if (2 * R < nrows) {  // output 0 is complete after row 2R (slot 0)
+            store(y0, acc[0]);
+            acc[0][0] = acc[0][1] = acc[0][2] = acc[0][3] = 0.0f;
+        }
+        for (int base = NS; base < nrows; base += NS) {
+#pragma unroll
+            for (int u = 0; u < NS; ++u) {
+                const int qq = base + u;
+                if (qq < nrows) {
+                    row(qq, u, 2 * R);
+                    const int jj = qq - 2 * R;  // complete output
+                    const int done = (u + 1) % NS;
+                    store(y0 + jj, acc[done]);
+                    acc[done][0] = acc[done][1] = acc[done][2] = acc[done][3] = 0.0f;
+                }
+            }
+        }
+    }
+}
+
 // Persistent form: CTA b processes tiles b, b + gridDim.x, ...; while it
 // computes one tile it prefetches the next into the other staging buffer
 // with cp.async, so the FMA pipe never waits for a synchronous load phase.
@@ -269,9 +412,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int k = threadIdx.x; k < KT; k += blockDim.x) wsm[k] = wt.w[k];
     }
     unsigned char *base = smem_raw + weight_smem_bytes<T, KT>();
-    const int H = BY + 2 * t * R, W = BX + 2 * t * R;
-    const size_t buf = (size_t)H * W;
-    T *stage[2] = {reinterpret_cast<T *>(base), reinterpret_cast<T *>(base) + buf};
+    const int H = BY + 2 * t * R, W = BX + 2 * t * R, P = row_pitch<T>(W);
+    const size_t buf = buf_elems<T>(H, W);
+    T *const stage0 = reinterpret_cast<T *>(base), *const stage1 = stage0 + buf;
     T *work = reinterpret_cast<T *>(base) + 2 * buf;
     const int64_t ny = Ey - 2 * R, nx = Ex - 2 * R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -297,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const T *g = in + Y0 * Ex + X0;
             for (int y = warp; y < H; y += nwarps) {
                 const T *grow = g + y * Ex;
-                T *srow = dst + y * W;
+                T *srow = dst + y * P;
                 for (int x = lane; x < W; x += 32) cp_async_elem<sizeof(T)>(srow + x, grow + x, true);
             }
             return;
@@ -308,24 +451,24 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int x = lane; x < W; x += 32) {
                 const int64_t gx = X0 + x;
                 const bool ok = rowok && gx >= 0 && gx < Ex;
-                cp_async_elem<sizeof(T)>(dst + y * W + x, ok ? in + gy * Ex + gx : in, ok);
+                cp_async_elem<sizeof(T)>(dst + y * P + x, ok ? in + gy * Ex + gx : in, ok);
             }
         }
     };
 
     int cur = 0;
-    if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, stage[0]);
+    if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, stage0);
     cp_async_commit();
     for (int id = blockIdx.x; id < ntiles; id += gridDim.x) {
         const int nid = id + gridDim.x;
-        if (nid < ntiles) prefetch(nid, stage[cur ^ 1]);
+        if (nid < ntiles) prefetch(nid, cur ? stage0 : stage1);
         cp_async_commit();
         cp_async_wait_group<1>();  // this tile's copies (all but the newest group) have landed
         __syncthreads();
         int64_t Y0, X0;
         origin(id, &Y0, &X0);
 
-        T *src = stage[cur], *dst = work;
+        T *src = cur ? stage1 : stage0, *dst = work;
         for (int s = 1; s <= t; ++s) {
             const int lo = s * R;
             const int hiY = H - s * R, hiX = W - s * R;
@@ -334,12 +477,24 @@ __global__ void __launch_bounds__(kThreads, 2)
             const bool last = s == t;
             if constexpr (sizeof(T) == 4) {
                 const bool all_int = Y0 + lo >= R && Y0 + hiY <= Ey - R && X0 + lo >= R && X0 + hiX <= Ex - R;
-                if (((lo - R) & 1) == 0)
-                    f32_substep<SHAPE, R, 0>(src, dst, out, wt, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
-                                             ring.band);
-                else
-                    f32_substep<SHAPE, R, 1>(src, dst, out, wt, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
-                                             ring.band);
+                switch ((lo - R) & 3) {  // offset of the first window within its 16-byte chunk
+                case 0:
+                    f32_substep4<SHAPE, R, 0>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
+                                              ring.band);
+                    break;
+                case 1:
+                    f32_substep4<SHAPE, R, 1>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
+                                              ring.band);
+                    break;
+                case 2:
+                    f32_substep4<SHAPE, R, 2>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
+                                              ring.band);
+                    break;
+                default:
+                    f32_substep4<SHAPE, R, 3>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,
+                                              ring.band);
+                    break;
+                }
                 __syncthreads();
                 T *tmp = src;
                 src = dst;
@@ -356,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int q = 0; q < V + 2 * R; ++q) {
                     const int yy = y0 - R + q;
                     if (yy < H) {
-                        const T *row = src + yy * W + x;
+                        const T *row = src + yy * P + x;
                         T v[2 * R + 1];
 #pragma unroll
                         for (int c = 0; c < 2 * R + 1; ++c) v[c] = row[c - R];
@@ -390,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                             }
                             if (keep) out[gy * Ex + gx] = acc[j];
                         } else {
-                            dst[y * W + x] = interior ? acc[j] : src[y * W + x];
+                            dst[y * P + x] = interior ? acc[j] : src[y * P + x];
                         }
                     }
                 }

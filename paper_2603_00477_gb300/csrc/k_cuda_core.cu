@@ -69,8 +69,9 @@ stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int ban
     if (band > 0 || p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
     const int BY = tile[1], BX = tile[2];
     const size_t H = BY + 2 * t * R, W = BX + 2 * t * R;
+    const size_t bufb = cu::buf_elems<T>((int)H, (int)W) * sizeof(T);
     // weights (FP64) + two staging buffers (+ a work buffer for t > 1)
-    const size_t smem = cu::weight_smem_bytes<T, cu::Taps<SHAPE, 2, R>::K>() + H * W * sizeof(T) * (t > 1 ? 3 : 2);
+    const size_t smem = cu::weight_smem_bytes<T, cu::Taps<SHAPE, 2, R>::K>() + bufb * (t > 1 ? 3 : 2);
     if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
     auto kern = cu::cu2d_sweep<T, SHAPE, R, kV<T>>;
     stencil_status s = ensure_smem((const void *)kern, smem, &cached);
