@@ -276,6 +276,15 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
         plan.close()
     plain = max(r["gstencils"] for r in rows if r["path"] == "cuda_core")
     best = max(rows, key=lambda r: r["gstencils"])
+    # CUDA cores vs tensor cores at each t: the model's winner and the measured one
+    crossover = []
+    for t in (1, 2, 3, 4):
+        at = [r for r in rows if r["t"] == t and r["precision"] in ("native", "tf32")]
+        m = max(at, key=lambda r: r["model_gstencils"])
+        g = max(at, key=lambda r: r["gstencils"])
+        crossover.append({"t": t, "model_winner": m["path"], "measured_winner": g["path"],
+                          "cuda_core_gstencils": next(r["gstencils"] for r in at if r["path"] == "cuda_core"),
+                          "best_tensor_gstencils": max(r["gstencils"] for r in at if r["path"] != "cuda_core")})
 
     # error growth: FP64 reference states every `every` steps (kept on the GPU)
     ref_plan = B.Plan("box", 2, 2, w, "f64", dims, 0)
@@ -319,7 +328,8 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
     return {"workload": f"Box-2D2R F32 16384x16384, sine-mode field, {steps} steps per timed run; "
                         f"error every {every} steps to {horizon}",
             "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests)",
-            "plain_fp32_cuda_core_gstencils": plain, "best": best, "rows": rows, "errors": errors}
+            "plain_fp32_cuda_core_gstencils": plain, "best": best, "crossover": crossover, "rows": rows,
+            "errors": errors}
 
 
 def batched_leg(B, inputs, stream, steps=20, ngrids=512):
@@ -375,7 +385,28 @@ def batched_leg(B, inputs, stream, steps=20, ngrids=512):
     sec_loop = _time_runs(loop, stream, reps=2)
     for p in plans:
         p.close()
+    # error of the tuned batched result after `steps` steps against the same
+    # grids run as an FP64 batch (FP64 CUDA cores, held within 1e-12 of the
+    # oracle by the GPU tests)
+    with torch.cuda.stream(side):
+        batch.run(ins, outs, steps, stream=side, graph=True)
+    side.synchronize()
     batch.close()
+    worst = 0.0
+    chunk = 128
+    for lo in range(0, len(probs), chunk):
+        sub = list(range(lo, min(lo + chunk, len(probs))))
+        bb = B.Batch([probs[i] for i in sub], "f64", 0)
+        i64 = [ins[i].double() for i in sub]
+        o64 = [torch.empty_like(a) for a in i64]
+        bb.run(i64, o64, steps)
+        torch.cuda.synchronize()
+        for k, i in enumerate(sub):
+            ref = o64[k]
+            d = float((outs[i].double() - ref).abs().max() / ref.abs().max().clamp_min(1e-300))
+            worst = max(worst, d)
+        bb.close()
+        del i64, o64
     del ins, outs
     torch.cuda.empty_cache()
     return {"workload": f"{len(probs)} FP32 grids, sides log-uniform in [64, 4096], Star-2D1R/Star-2D2R/Box-2D1R/Box-2D3R, "
@@ -385,6 +416,7 @@ def batched_leg(B, inputs, stream, steps=20, ngrids=512):
             "persistent_graph_model_choice_gstencils": pts * steps / sec_model / 1e9,
             "per_grid_loop_gstencils": pts * steps / sec_loop / 1e9,
             "per_grid_loop_launches": loop_launches, "persistent_graph_kernel_launches": graph_launches,
+            "max_rel_linf_vs_fp64": worst,
             "autotune": {"classes": len(chosen), "candidates_measured": sum(1 for q in tune if q["measured_gstencils"] > 0),
                          "seconds": tune_s, "grids_per_choice": picks}}
 

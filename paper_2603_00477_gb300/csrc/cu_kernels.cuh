@@ -278,8 +278,8 @@ __device__ __forceinline__ void f32_substep4(const float *__restrict__ src, floa
     constexpr int NL = (NV + 3) / 4;       // 16-byte loads per row
     const int cw = hiX - lo, ch = hiY - lo;
     const int nquads = (cw + 3) / 4;
-    // strips of >= 8 rows, enough of them to give every thread work
-    const int nstrips = max(1, min((ch + 7) / 8, (int)((blockDim.x + nquads - 1) / nquads)));
+    // enough strips to give every thread a work item, each of >= 4 rows
+    const int nstrips = max(1, min(max(1, ch / 4), (int)((blockDim.x + nquads - 1) / nquads)));
     const int S = (ch + nstrips - 1) / nstrips;
     const int64_t ny = Ey - 2 * R, nx = Ex - 2 * R;
     const bool fast = all_interior && band == 0;

@@ -80,7 +80,7 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
 #pragma unroll
     for (int k = 0; k < KT; ++k) w[k] = wg[k];
     const int BY = G.by, BX = G.bx;
-    const int H = BY + 2 * ts * R, W = BX + 2 * ts * R;
+    const int H = BY + 2 * ts * R, W = BX + 2 * ts * R, P = W;  // W is even
     T *bufA = reinterpret_cast<T *>(smem);
     T *bufB = bufA + (size_t)H * W;
     const int tby = tile / G.ntx, tbx = tile % G.ntx;
@@ -94,7 +94,7 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
         const bool rowok = gy >= 0 && gy < Ey;
         for (int x = lane; x < W; x += 32) {
             const int64_t gx = X0 + x;
-            bufA[y * W + x] = (rowok && gx >= 0 && gx < Ex) ? ld_l2(src_g + gy * Ex + gx) : T(0);
+            bufA[y * P + x] = (rowok && gx >= 0 && gx < Ex) ? ld_l2(src_g + gy * Ex + gx) : T(0);
         }
     }
     __syncthreads();
@@ -109,8 +109,8 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
             if (gy >= R && gy < Ey - R && gx >= R && gx < Ex - R) continue;  // interior
             const int64_t iy = min(max(gy - R, (int64_t)0), ny - 1), ix = min(max(gx - R, (int64_t)0), nx - 1);
             if (iy / BY != tby || ix / BX != tbx) continue;
-            outp[gy * Ex + gx] = bufA[i];
-            if (ppp) ppp[gy * Ex + gx] = bufA[i];
+            outp[gy * Ex + gx] = bufA[y * P + x];
+            if (ppp) ppp[gy * Ex + gx] = bufA[y * P + x];
         }
     }
 
@@ -129,10 +129,10 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
             for (int k = 0; k < KT; ++k) wrs.w[k] = w[k];
             const bool all_int = Y0 + lo >= R && Y0 + hiY <= Ey - R && X0 + lo >= R && X0 + hiX <= Ex - R;
             if (((lo - R) & 1) == 0)
-                cu::f32_substep<SHAPE, R, 0>(src, dst, dst_g, wrs, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last,
+                cu::f32_substep<SHAPE, R, 0>(src, dst, dst_g, wrs, P, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last,
                                                 all_int, 0);
             else
-                cu::f32_substep<SHAPE, R, 1>(src, dst, dst_g, wrs, W, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last,
+                cu::f32_substep<SHAPE, R, 1>(src, dst, dst_g, wrs, P, H, lo, hiY, hiX, Y0, X0, Ey, Ex, last,
                                                 all_int, 0);
             __syncthreads();
             T *tmp = src;
@@ -150,7 +150,7 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
             for (int q = 0; q < V + 2 * R; ++q) {
                 const int yy = y0 - R + q;
                 if (yy < H) {
-                    const T *row = src + yy * W + x;
+                    const T *row = src + yy * P + x;
                     T v[2 * R + 1];
 #pragma unroll
                     for (int c = 0; c < 2 * R + 1; ++c) v[c] = row[c - R];
@@ -178,7 +178,7 @@ __device__ void run_item(const GridDev &G, const T *__restrict__ wg, const T *sr
                     if (last) {
                         if (interior) dst_g[gy * Ex + gx] = acc[j];
                     } else {
-                        dst[y * W + x] = interior ? acc[j] : src[y * W + x];
+                        dst[y * P + x] = interior ? acc[j] : src[y * P + x];
                     }
                 }
             }
@@ -283,6 +283,16 @@ struct stencil_batch {
 namespace gbs {
 namespace {
 
+// Shared memory of one work item (a staging and a work buffer of the tile
+// grown by t r), and the budget every item of a batch keeps to: the launch
+// takes the largest item's size, and three CTAs per SM need <= ~74 KB each.
+constexpr size_t kBatchItemSmem = 74 * 1024;
+
+size_t batch_item_smem(int by, int bx, int t, int r, size_t es)
+{
+    return (size_t)(by + 2 * t * r) * (bx + 2 * t * r) * es * 2;
+}
+
 struct Layout {
     size_t grids_off, items_off, w_off, done_off, ctl_off, pp_off, total;
     int nitems, ndone;
@@ -365,7 +375,7 @@ stencil_status launch_batch(stencil_batch *b, const Layout &L, const void *const
     for (auto &g : b->grids) {
         if (!g.on_cu()) continue;
         const int R = g.plan.pat.r, t = g.plan.t;
-        smem = std::max(smem, (size_t)(g.plan.tile[1] + 2 * t * R) * (g.plan.tile[2] + 2 * t * R) * es * 2);
+        smem = std::max(smem, batch_item_smem(g.plan.tile[1], g.plan.tile[2], t, R, es));
     }
     static int cached64 = 0, cached32 = 0;
     const void *fn = b->dtype == STENCIL_F64 ? (const void *)bt::batch_sweeps<double> : (const void *)bt::batch_sweeps<float>;
@@ -457,15 +467,14 @@ stencil_status check_run_args(stencil_batch *b, const void *const *ins, void *co
 }
 
 // One staging + one work buffer per work item: the CUDA-core default tile,
-// halved until the grown tile pair fits in ~100 KB.
+// halved until the grown tile pair fits the per-item budget.
 void batch_tile(Plan *p)
 {
     int tile[3];
     cu_default_tile(*p, p->t, tile);
     for (;;) {
-        const size_t bytes =
-            (size_t)(tile[1] + 2 * p->t * p->pat.r) * (tile[2] + 2 * p->t * p->pat.r) * p->elem_bytes() * 2;
-        if (bytes <= 100 * 1024 || (tile[1] <= 16 && tile[2] <= 16)) break;
+        const size_t bytes = batch_item_smem(tile[1], tile[2], p->t, p->pat.r, p->elem_bytes());
+        if (bytes <= kBatchItemSmem || (tile[1] <= 16 && tile[2] <= 16)) break;
         if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
     }
     for (int k = 0; k < 3; k++) p->tile[k] = tile[k];
@@ -776,7 +785,7 @@ stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *i
         for (int t = 1; t <= 4; t++)
             for (auto &tl : kTuneTiles) {
                 const int ty = tl[0], tx = tl[1];
-                if ((size_t)(ty + 2 * t * r) * (tx + 2 * t * r) * es * 2 > 100 * 1024) continue;
+                if (batch_item_smem(ty, tx, t, r, es) > kBatchItemSmem) continue;
                 if (ty > 2 * std::max<int64_t>(16, maxy) || tx > 2 * std::max<int64_t>(64, maxx)) continue;
                 Cand c{STENCIL_PATH_CUDA_CORE, STENCIL_PREC_NATIVE, t, ty, tx, 0, 0};
                 Plan q = base;
