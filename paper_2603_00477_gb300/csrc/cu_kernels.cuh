@@ -399,7 +399,7 @@ __host__ __device__ constexpr int weight_smem_bytes()
 }
 
 template <typename T, int SHAPE, int R, int V>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && R <= 3) ? 3 : 2)
     cu2d_sweep(const T *__restrict__ in, T *__restrict__ out,
                const __grid_constant__ Weights<T, Taps<SHAPE, 2, R>::K> wt, int64_t Ey, int64_t Ex, int BY, int BX,
                int t, const Ring ring, int ntiles)
