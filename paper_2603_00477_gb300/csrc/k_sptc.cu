@@ -84,7 +84,7 @@ constexpr int kSpTY = 128, kSpTX = 64;
 // offset rho the B fragments (one 16-byte load per instruction) are loaded
 // once, one row ahead, and fed to every (accumulator y0, line a) with
 // y0 + a = rho.
-template <int NS, int NL>
+template <int NS, int NL, bool FULL>
 __device__ __forceinline__ void sp_pass(float (&acc)[8][4], const float *Tw, int a_lo, int RP, const int (&boff0)[NS],
                                         const int (&boff1)[NS], int g, const float4 *Af, const uint32_t *Em,
                                         const unsigned char *mask, int lane)
@@ -94,7 +94,7 @@ __device__ __forceinline__ void sp_pass(float (&acc)[8][4], const float *Tw, int
     unsigned mk[NL];
 #pragma unroll
     for (int al = 0; al < NL; al++) {
-        mk[al] = mask[a_lo + al];
+        mk[al] = FULL ? 0xFu : mask[a_lo + al];
 #pragma unroll
         for (int s = 0; s < NS; s++) {
             const int idx = ((a_lo + al) * NS + s) * 32 + lane;
@@ -108,26 +108,24 @@ __device__ __forceinline__ void sp_pass(float (&acc)[8][4], const float *Tw, int
 #pragma unroll
         for (int s = 0; s < NS; s++) Bv[s] = *reinterpret_cast<const float4 *>(srow + (swz ? boff1[s] : boff0[s]));
     };
-    float4 Bc[NS], Bn[NS];
-    loadB(a_lo, Bc);
+    float4 Bb[2][NS];  // row rr in Bb[rr & 1], row rr + 1 loaded ahead into the other
+    loadB(a_lo, Bb[0]);
 #pragma unroll
     for (int rr = 0; rr < NL + 7; rr++) {
-        if (rr + 1 < NL + 7) loadB(a_lo + rr + 1, Bn);
+        if (rr + 1 < NL + 7) loadB(a_lo + rr + 1, Bb[(rr + 1) & 1]);
 #pragma unroll
         for (int s = 0; s < NS; s++) {
 #pragma unroll
             for (int y0 = 0; y0 < 8; y0++) {
                 const int al = rr - y0;
                 if (al < 0 || al >= NL) continue;
-                if ((mk[al] >> s) & 1u) mma_sp(acc[y0], A[al][s], Bc[s], E[al][s]);
+                if (FULL || ((mk[al] >> s) & 1u)) mma_sp(acc[y0], A[al][s], Bb[rr & 1][s], E[al][s]);
             }
         }
-#pragma unroll
-        for (int s = 0; s < NS; s++) Bc[s] = Bn[s];
     }
 }
 
-template <int NS, int LC>
+template <int NS, int LC, bool FULL>
 __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__ in, float *__restrict__ out,
                                                        const __grid_constant__ SpParams p, int ntiles, int ntx)
 {
@@ -232,12 +230,12 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
         const float *Tw = T + (size_t)(64 * wb + 8 * g) * RP;
         int a_lo = 0;
         for (; a_lo + LC <= lines; a_lo += LC)
-            sp_pass<NS, LC>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane);
+            sp_pass<NS, LC, FULL>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane);
         switch (lines - a_lo) {  // the last, partial pass: no predicated-off MMAs
-        case 1: sp_pass<NS, 1>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
-        case 2: if constexpr (LC > 2) sp_pass<NS, 2>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
-        case 3: if constexpr (LC > 3) sp_pass<NS, 3>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
-        case 4: if constexpr (LC > 4) sp_pass<NS, 4>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 1: sp_pass<NS, 1, FULL>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 2: if constexpr (LC > 2) sp_pass<NS, 2, FULL>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 3: if constexpr (LC > 3) sp_pass<NS, 3, FULL>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
+        case 4: if constexpr (LC > 4) sp_pass<NS, 4, FULL>(acc, Tw, a_lo, RP, boff0, boff1, g, Af, Em, p.mask, lane); break;
         default: break;
         }
 
@@ -274,7 +272,7 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
     cp_async_wait0();
 }
 
-template <int NS, int LC>
+template <int NS, int LC, bool FULL>
 stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t ny, int64_t nx, cudaStream_t st)
 {
     static int cached = 0;
@@ -286,7 +284,7 @@ stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t 
     sp2.nbuf = table + 2 * tile <= 112 * 1024 ? 2 : 1;
     const size_t smem = table + sp2.nbuf * tile;
     if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core tile does not fit in shared memory");
-    auto kern = sptc2d_sweep<NS, LC>;
+    auto kern = sptc2d_sweep<NS, LC, FULL>;
     stencil_status s = ensure_smem((const void *)kern, smem, &cached);
     if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0, per_sm = 0;
@@ -334,10 +332,15 @@ stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t
     sp.Ey = p.ext[1];
     sp.Ex = p.ext[2];
     stencil_status s;
-    switch (L.ns) {
-    case 2: s = launch_ns<2, 5>(sp, in, out, p.dims[1], p.dims[2], st); break;
-    case 3: s = launch_ns<3, 4>(sp, in, out, p.dims[1], p.dims[2], st); break;
-    case 4: s = launch_ns<4, 2>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    bool full = true;  // every line issues every instruction (no mask tests)
+    for (int a = 0; a < lines; a++) full = full && L.mask[a] == (1 << L.ns) - 1;
+    switch (L.ns * 2 + (full ? 1 : 0)) {
+    case 4: s = launch_ns<2, 5, false>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 5: s = launch_ns<2, 5, true>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 6: s = launch_ns<3, 4, false>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 7: s = launch_ns<3, 4, true>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 8: s = launch_ns<4, 2, false>(sp, in, out, p.dims[1], p.dims[2], st); break;
+    case 9: s = launch_ns<4, 2, true>(sp, in, out, p.dims[1], p.dims[2], st); break;
     default: return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core path: layout");
     }
     if (s != STENCIL_OK || t == 1) return s;
