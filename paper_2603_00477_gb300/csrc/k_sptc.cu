@@ -39,6 +39,8 @@ struct SpParams {
     int cf[2 * kSpMaxNs], cs[2 * kSpMaxNs], bchunk[4 * kSpMaxNs];
     unsigned char mask[kSpMaxLines];
     int R, rh, band, lines, sigma, pitch_q, rl, nbuf;
+    int vec16;  // 1: rows of the stored grid are 16-byte multiples and tiles start xshift columns left of
+    int xshift; //    the interior so that every staged 16-byte chunk is aligned in global memory
     int64_t Ey, Ex;
 };
 
@@ -64,6 +66,12 @@ __device__ __forceinline__ void cp_async4(float *smem_dst, const float *gmem_src
 {
     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(gmem_src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float *smem_dst, const float *gmem_src, bool valid)
+{
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "r"(valid ? 16 : 0)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -173,20 +181,31 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
     const bool dbl = p.nbuf == 2;
 
     // Each thread copies (and later rounds) the same elements of every tile:
-    // rows warp + 8i, columns lane + 32k of the staged window.
+    // rows warp + 8i and, in 16-byte mode, 16-byte chunks lane + 32k, else
+    // columns lane + 32k of the staged window.
     auto stage = [&](int tile, float *buf) {
         const int ty = tile / ntx, tx = tile - ty * ntx;
-        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY - R, X0 = p.rh + (int64_t)tx * kSpTX - R;
+        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY - R, X0 = p.rh - p.xshift + (int64_t)tx * kSpTX - R;
         const bool inside = Y0 >= 0 && Y0 + H <= p.Ey && X0 >= 0 && X0 + RL <= Ex;
         for (int i = warp; i < H; i += 8) {
             const int sw = ((i >> 3) & 1) ? p.sigma : 0;
-            float *dst = buf + (size_t)i * RP + 4 * ((lane >> 2) ^ sw) + (lane & 3);
             const int64_t gy = Y0 + i;
+            const bool rok = gy >= 0 && gy < p.Ey;
+            if (p.vec16) {
+                float *drow = buf + (size_t)i * RP;
+                const float *srow = in + (rok ? gy : 0) * Ex;
+                for (int c = lane; 4 * c < RL; c += 32) {
+                    const int64_t gx = X0 + 4 * c;  // a multiple of 4: the chunk is wholly inside or outside
+                    const bool ok = rok && gx >= 0 && gx < Ex;
+                    cp_async16(drow + 4 * (c ^ sw), ok ? srow + gx : in, ok);
+                }
+                continue;
+            }
+            float *dst = buf + (size_t)i * RP + 4 * ((lane >> 2) ^ sw) + (lane & 3);
             if (inside) {
                 const float *src = in + gy * Ex + X0 + lane;
                 for (int j = 0; j + lane < RL; j += 32) cp_async4(dst + j, src + j, true);
             } else {
-                const bool rok = gy >= 0 && gy < p.Ey;
                 for (int j = 0; j + lane < RL; j += 32) {
                     const int64_t gx = X0 + lane + j;
                     const bool ok = rok && gx >= 0 && gx < Ex;
@@ -198,6 +217,19 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
     auto round_own = [&](float *buf) {
         for (int i = warp; i < H; i += 8) {
             const int sw = ((i >> 3) & 1) ? p.sigma : 0;
+            if (p.vec16) {
+                float *drow = buf + (size_t)i * RP;
+                for (int c = lane; 4 * c < RL; c += 32) {
+                    float4 *q4 = reinterpret_cast<float4 *>(drow + 4 * (c ^ sw));
+                    float4 v = *q4;
+                    v.x = cvt_tf32(v.x);
+                    v.y = cvt_tf32(v.y);
+                    v.z = cvt_tf32(v.z);
+                    v.w = cvt_tf32(v.w);
+                    *q4 = v;
+                }
+                continue;
+            }
             float *dst = buf + (size_t)i * RP + 4 * ((lane >> 2) ^ sw) + (lane & 3);
             for (int j = 0; j + lane < RL; j += 32) dst[j] = cvt_tf32(dst[j]);
         }
@@ -208,7 +240,7 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
     cp_async_commit();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ty = tile / ntx, tx = tile - ty * ntx;
-        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY, X0 = p.rh + (int64_t)tx * kSpTX;
+        const int64_t Y0 = p.rh + (int64_t)ty * kSpTY, X0 = p.rh - p.xshift + (int64_t)tx * kSpTX;
         float *T = S + cur * tile_floats;
         if (dbl) {
             const int nxt = tile + gridDim.x;
@@ -293,7 +325,7 @@ stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t 
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     if (e != cudaSuccess) return cuda_fail(e, "sptc2d_sweep occupancy");
     if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core kernel cannot be resident");
-    const int64_t nty = (ny + kSpTY - 1) / kSpTY, ntx = (nx + kSpTX - 1) / kSpTX, ntiles = nty * ntx;
+    const int64_t nty = (ny + kSpTY - 1) / kSpTY, ntx = (nx + sp.xshift + kSpTX - 1) / kSpTX, ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
     kern<<<grid, 256, smem, st>>>((const float *)in, (float *)out, sp2, (int)ntiles, (int)ntx);
@@ -331,6 +363,12 @@ stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t
     sp.rl = L.rl;
     sp.Ey = p.ext[1];
     sp.Ex = p.ext[2];
+    // 16-byte staging when every stored row is a 16-byte multiple and the
+    // input pointer is 16-byte aligned: the first tile then starts xshift
+    // columns left of the interior (its outputs there are skipped) so that
+    // each tile's staged window starts on a 16-byte boundary
+    sp.vec16 = (p.ext[2] % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
+    sp.xshift = sp.vec16 ? (int)(((r - R) % 4 + 4) % 4) : 0;
     stencil_status s;
     bool full = true;  // every line issues every instruction (no mask tests)
     for (int a = 0; a < lines; a++) full = full && L.mask[a] == (1 << L.ns) - 1;
