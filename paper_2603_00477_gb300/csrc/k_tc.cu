@@ -48,6 +48,8 @@ struct TcParams {
     unsigned char kb_lo[kTcMaxLines], kb_hi[kTcMaxLines];
     int R, rh, band, nkb, hs, nch;
     int debug_unmet;  // test hook: first wait on an mbarrier phase that never completes
+    int vec16;        // tc2d_ws: stage 16-byte chunks (stored rows are 16-byte multiples)
+    int xshift;       // tc2d_ws: tiles start xshift columns left of column 0 (aligned windows)
     int64_t Ey, Ex;
 };
 
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(288, 1)
     };
     auto origin = [&](int id, int64_t *Y0, int64_t *X0) {
         *Y0 = rh + (int64_t)(id / ntx) * TM;
-        *X0 = (int64_t)(id % ntx) * TX;
+        *X0 = (int64_t)(id % ntx) * TX - p.xshift;
     };
 
     if (warp == 8) {
@@ -425,6 +427,24 @@ __global__ void __launch_bounds__(288, 1)
         auto prefetch = [&](int id, float *dst) {
             int64_t Y0, X0;
             origin(id, &Y0, &X0);
+            if (p.vec16) {
+                // one 16-byte copy per (row, chunk column); X0 - R is a multiple of 4,
+                // so each chunk lies wholly inside or wholly outside its row
+                for (int row = warp; row < rows; row += 8) {
+                    const int64_t gy = Y0 - R + row;
+                    const bool rowok = gy >= 0 && gy < Ey;
+                    const float *grow = in + (rowok ? gy : 0) * Ex;
+                    for (int c = lane; c < NCH; c += 32) {
+                        const int64_t gx = X0 - R + 4 * c;
+                        const bool ok = rowok && gx >= 0 && gx < Ex;
+                        const uint32_t d = smem_u32(dst) + (uint32_t)(c * HS + row) * 16;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d),
+                                     "l"(ok ? grow + gx : in), "r"(ok ? 16 : 0)
+                                     : "memory");
+                    }
+                }
+                return;
+            }
             for (int row = warp; row < rows; row += 8) {
                 const int64_t gy = Y0 - R + row;
                 const bool rowok = gy >= 0 && gy < Ey;
@@ -459,9 +479,14 @@ __global__ void __launch_bounds__(288, 1)
                     const int64_t gx0 = X0 + q * TN_ + h * 8;
                     float *dst = out + gy * Ex + gx0;
                     const bool fullrow = gx0 >= rh + p.band && gx0 + 7 < Ex - rh - p.band;
-                    if (fullrow && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+                    const uintptr_t al = reinterpret_cast<uintptr_t>(dst) & 15;
+                    if (fullrow && al == 0) {
                         reinterpret_cast<float4 *>(dst)[0] = make_float4(f[0], f[1], f[2], f[3]);
                         reinterpret_cast<float4 *>(dst)[1] = make_float4(f[4], f[5], f[6], f[7]);
+                    } else if (fullrow && (al & 7) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            reinterpret_cast<float2 *>(dst)[j] = make_float2(f[2 * j], f[2 * j + 1]);
                     } else {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
@@ -485,14 +510,16 @@ __global__ void __launch_bounds__(288, 1)
                 ok = false;
                 break;
             }
-            // round to TF32 in place (and split off the lo part)
-            const int words = (int)(a_bytes / 4);
-            float *A = Ahi[b], *L = Alo[b];
-            for (int i = tid; i < words; i += 256) {
-                const float u = A[i];
-                const float hi = to_tf32(u);
+            // round to TF32 in place (and split off the lo part), 16 bytes at a time
+            const int quads = (int)(a_bytes / 16);
+            float4 *A = reinterpret_cast<float4 *>(Ahi[b]), *L = reinterpret_cast<float4 *>(Alo[b]);
+            for (int i = tid; i < quads; i += 256) {
+                const float4 u = A[i];
+                const float4 hi = make_float4(to_tf32(u.x), to_tf32(u.y), to_tf32(u.z), to_tf32(u.w));
                 A[i] = hi;
-                if (SPLIT) L[i] = to_tf32(u - hi);
+                if (SPLIT)
+                    L[i] = make_float4(to_tf32(u.x - hi.x), to_tf32(u.y - hi.y), to_tf32(u.z - hi.z),
+                                       to_tf32(u.w - hi.w));
             }
             fence_proxy_async_smem();
             mbar_arrive(&full[b]);
@@ -694,7 +721,12 @@ stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t nty = (p.dims[1] + TM - 1) / TM, ntx = (p.ext[2] + TX - 1) / TX;
+    // 16-byte staging when every stored row is a 16-byte multiple: the tile
+    // grid then starts xshift columns left of column 0 so that each staged
+    // window (tile start - R) begins on a 16-byte boundary
+    tp.vec16 = (p.ext[2] % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
+    tp.xshift = tp.vec16 ? (4 - R % 4) % 4 : 0;
+    const int64_t nty = (p.dims[1] + TM - 1) / TM, ntx = (p.ext[2] + tp.xshift + TX - 1) / TX;
     const int64_t ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
