@@ -80,6 +80,9 @@ struct Ring {
     int top_w;       // tile rows touching the top band
     int cols_lr;     // tile columns taken in the other rows: min(ntx, left_w + right cols)
     int left_w;      // tile columns touching the left band
+    int xshift;      // band 0, FP32: the tile grid starts xshift columns further left so that
+                     // every staged window begins on a 16-byte boundary (then vec16 = 1)
+    int vec16;       // stage interior tiles with 16-byte copies
 };
 
 // Tile id -> (tile row, tile column): first the whole tile rows (the top_w
@@ -428,13 +431,23 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && R <= 3) ? 3 : 2)
             bx = id % ring.ntx;
         }
         *Y0 = R + (int64_t)by * BY - (int64_t)t * R;
-        *X0 = R + (int64_t)bx * BX - (int64_t)t * R;
+        *X0 = R + (int64_t)bx * BX - (int64_t)t * R - ring.xshift;
     };
     // Stage the dependency region of a tile; cells outside the stored array
     // are zero-filled and never used by an interior point.
     auto prefetch = [&](int id, T *dst) {
         int64_t Y0, X0;
         origin(id, &Y0, &X0);
+        if (sizeof(T) == 4 && ring.vec16 && Y0 >= 0 && X0 >= 0 && Y0 + H <= Ey && X0 + P <= Ex) {
+            // 16-byte copies: X0, the row length and the input are 16-byte aligned
+            const T *g = in + Y0 * Ex + X0;
+            for (int y = warp; y < H; y += nwarps) {
+                const T *grow = g + y * Ex;
+                T *srow = dst + y * P;
+                for (int c = lane; 4 * c < W; c += 32) cp_async_elem<16>(srow + 4 * c, grow + 4 * c, true);
+            }
+            return;
+        }
         if (Y0 >= 0 && X0 >= 0 && Y0 + H <= Ey && X0 + W <= Ex) {
             // the whole region lies in the stored array: no per-element tests
             const T *g = in + Y0 * Ex + X0;

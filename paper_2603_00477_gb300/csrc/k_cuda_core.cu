@@ -84,7 +84,15 @@ stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int ban
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const cu::Ring ring = make_ring(p.dims[1], p.dims[2], BY, BX, band);
+    cu::Ring ring = make_ring(p.dims[1], p.dims[2], BY, BX, band);
+    if (sizeof(T) == 4 && band == 0 && p.ext[2] % 4 == 0 && BX % 4 == 0 &&
+        reinterpret_cast<uintptr_t>(in) % 16 == 0) {
+        // shift the tile grid left so that each staged window starts on a
+        // 16-byte boundary (window start = R + bx BX - t R - xshift)
+        ring.xshift = (int)(((int64_t)R * (1 - t) % 4 + 4) % 4);
+        ring.vec16 = 1;
+        ring.ntx = (int)((p.dims[2] + ring.xshift + BX - 1) / BX);
+    }
     const int64_t ntiles = ring_count(ring);
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
     const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
