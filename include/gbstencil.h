@@ -267,10 +267,13 @@ typedef struct {
     int path, precision, t;
     double model_gstencils;     /* the dispatcher's (model) prediction */
     double measured_gstencils;  /* point-updates/s / 1e9 on the caller's buffers */
+    int tile_y, tile_x;         /* the tile the candidate ran with */
 } stencil_tune_result;
 
 /* Autotuner seeded by the model: runs every (path, precision, t) the plan's
- * options allow, in the model's order, `reps` times `steps` steps on the
+ * options allow, in the model's order (2-D CUDA-core candidates also with the
+ * tiles 32x256, 64x128, 64x64, 32x128 and 128x64 unless a tile was set),
+ * `reps` times `steps` steps on the
  * caller's device buffers (after one warm-up run each), times them with CUDA
  * events on `stream`, and makes the fastest the plan's choice.  Uses the
  * plan's workspace like stencil_run; `out` is overwritten.  Writes up to

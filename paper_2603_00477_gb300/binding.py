@@ -71,7 +71,8 @@ class stencil_batch_tune_result(ctypes.Structure):
 
 class stencil_tune_result(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int), ("precision", ctypes.c_int), ("t", ctypes.c_int),
-                ("model_gstencils", ctypes.c_double), ("measured_gstencils", ctypes.c_double)]
+                ("model_gstencils", ctypes.c_double), ("measured_gstencils", ctypes.c_double),
+                ("tile_y", ctypes.c_int), ("tile_x", ctypes.c_int)]
 
 
 class stencil_model_in(ctypes.Structure):
@@ -298,7 +299,8 @@ def stencil_plan_autotune(plan: int, in_ptr: int, out_ptr: int, steps: int, reps
     _check(load().stencil_plan_autotune(plan, in_ptr, out_ptr, int(steps), int(reps), _stream_handle(stream), res,
                                         max_results, ctypes.byref(n)), "stencil_plan_autotune")
     return [{"path": PATH_NAMES[r.path], "precision": PREC_NAMES[r.precision], "t": r.t,
-             "model_gstencils": r.model_gstencils, "measured_gstencils": r.measured_gstencils}
+             "model_gstencils": r.model_gstencils, "measured_gstencils": r.measured_gstencils,
+             "tile": (r.tile_y, r.tile_x)}
             for r in res[:min(n.value, max_results)]]
 
 

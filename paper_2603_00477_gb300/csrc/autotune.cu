@@ -6,7 +6,8 @@
 // every candidate the plan's options allow on the caller's buffers, timed
 // with CUDA events on the caller's stream, and makes the fastest the plan's
 // choice.  Candidates are visited in the model's order, so the model seeds
-// the search and its prediction is reported next to each measurement.
+// the search and its prediction is reported next to each measurement; 2-D
+// CUDA-core candidates are also tried with several tile shapes.
 #include <algorithm>
 #include <vector>
 
@@ -37,16 +38,52 @@ extern "C" stencil_status stencil_plan_autotune(stencil_plan *plan, const void *
     const Plan saved = p;
     double best = -1;
     size_t best_i = 0;
+    int best_tile[2] = {0, 0};
     int n = 0;
+    // CUDA-core candidates of a 2-D plan are also tried with other tile shapes
+    // (the default first); the tile changes the redundant halo work of the
+    // overlapped temporal tiles and the occupancy
+    static const int kTiles2d[][2] = {{0, 0}, {32, 256}, {64, 128}, {64, 64}, {32, 128}, {128, 64}};
+    struct Trial {
+        size_t i;
+        int ty, tx;
+    };
+    std::vector<Trial> trials;
+    size_t def_i = (size_t)-1;
+    int def_tile[2] = {0, 0};
     for (size_t i = 0; i < paths.size(); i++) {
+        if (paths[i] == STENCIL_PATH_CUDA_CORE && saved.pat.d == 2 && !saved.req_tile[1]) {
+            for (auto &tl : kTiles2d) trials.push_back({i, tl[0], tl[1]});
+        } else {
+            trials.push_back({i, 0, 0});
+        }
+    }
+    for (const Trial &tr : trials) {
+        const size_t i = tr.i;
         Plan trial = saved;
         trial.req_path = paths[i];
         trial.req_precision = precs[i];
         trial.req_t = ts[i];
         trial.req_tile[0] = trial.req_tile[1] = trial.req_tile[2] = 0;
+        if (tr.ty) {
+            trial.req_tile[0] = 1;
+            trial.req_tile[1] = tr.ty;
+            trial.req_tile[2] = tr.tx;
+        }
         if (dispatch(&trial) != STENCIL_OK) continue;
+        if (!tr.ty) {  // the candidate's default tile, tried first
+            def_i = i;
+            def_tile[0] = trial.tile[1];
+            def_tile[1] = trial.tile[2];
+        } else if (def_i == i && trial.tile[1] == def_tile[0] && trial.tile[2] == def_tile[1]) {
+            continue;  // the default tile again
+        }
         p = trial;
         s = stencil_run(plan, in, out, steps, stream);  // warm-up
+        if (s == STENCIL_ERR_UNSUPPORTED && tr.ty) {  // this tile does not fit shared memory
+            s = STENCIL_OK;
+            continue;
+        }
         if (s != STENCIL_OK) break;
         cudaEventRecord(e0, st);
         for (int r = 0; r < reps && s == STENCIL_OK; r++) s = stencil_run(plan, in, out, steps, stream);
@@ -64,13 +101,17 @@ extern "C" stencil_status stencil_plan_autotune(stencil_plan *plan, const void *
             results[n].path = paths[i];
             results[n].precision = precs[i];
             results[n].t = ts[i];
-            results[n].model_gstencils = model[i];
+            results[n].model_gstencils = trial.info.predicted_gstencils;
             results[n].measured_gstencils = gst;
+            results[n].tile_y = trial.tile[1];
+            results[n].tile_x = trial.tile[2];
         }
         n++;
         if (gst > best) {
             best = gst;
             best_i = i;
+            best_tile[0] = tr.ty;
+            best_tile[1] = tr.tx;
         }
     }
     cudaEventDestroy(e0);
@@ -85,12 +126,16 @@ extern "C" stencil_status stencil_plan_autotune(stencil_plan *plan, const void *
     chosen.req_precision = precs[best_i];
     chosen.req_t = ts[best_i];
     chosen.req_tile[0] = chosen.req_tile[1] = chosen.req_tile[2] = 0;
+    if (best_tile[0]) {
+        chosen.req_tile[0] = 1;
+        chosen.req_tile[1] = best_tile[0];
+        chosen.req_tile[2] = best_tile[1];
+    }
     s = dispatch(&chosen);
     if (s != STENCIL_OK) {
         p = saved;
         return s;
     }
-    chosen.info.predicted_gstencils = model[best_i];
     p = chosen;
     return STENCIL_OK;
 }

@@ -33,11 +33,20 @@ def test_autotune_picks_fastest_and_runs_it(torch, shape, r, dtype, prec):
     res = plan.autotune(x, y, steps=4, reps=1)
     assert len(res) >= 2
     assert all(q["measured_gstencils"] > 0 and q["model_gstencils"] > 0 for q in res)
-    model = [q["model_gstencils"] for q in res]
-    assert model == sorted(model, reverse=True)  # visited in the model's order
+    # candidates are visited in the model's order (each first with its default tile)
+    firsts, seen = [], set()
+    for q in res:
+        key = (q["path"], q["precision"], q["t"])
+        if key not in seen:
+            seen.add(key)
+            firsts.append(q["model_gstencils"])
+    assert firsts == sorted(firsts, reverse=True)
     best = max(res, key=lambda q: q["measured_gstencils"])
     info = plan.info()
     assert (info["path_name"], info["precision_name"], info["t"]) == (best["path"], best["precision"], best["t"])
+    assert tuple(info["tile"][1:]) == tuple(best["tile"])
+    if best["path"] == "cuda_core":
+        assert len({q["tile"] for q in res if q["path"] == "cuda_core" and q["t"] == best["t"]}) >= 2
     if prec == "native":
         assert best["precision"] == "native"
     plan.run(x, y, 5)
@@ -47,6 +56,8 @@ def test_autotune_picks_fastest_and_runs_it(torch, shape, r, dtype, prec):
     if dtype == "f32":
         ref_plan.set_option("precision", best["precision"])
     ref_plan.set_option("path", best["path"])
+    if best["path"] == "cuda_core":
+        ref_plan.set_option("tile", f"{best['tile'][0]}x{best['tile'][1]}")
     z = torch.empty_like(x)
     ref_plan.run(x, z, 5)
     B.stencil_device_status()
