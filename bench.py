@@ -228,6 +228,25 @@ def traffic_record(kernel_key):
 
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest per-rank value (a duration): every rank gets the maximum.
+    Uses a CUDA tensor under NCCL and a CPU tensor under gloo."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world: int, points: int, steps_per_run: int, runs: int, seconds: float) -> float:
+    """Point-updates per second / 1e9 over all ranks: each rank runs its own
+    replica (weak scaling), the job takes the slowest rank's time."""
+    return world * points * steps_per_run * runs / seconds / 1e9
+
+
 def _time_runs(fn, stream, reps=3, warm=1):
     import torch
     for _ in range(warm):
@@ -523,11 +542,8 @@ def main():
     barrier()
     ms = e0.elapsed_time(e1)
     clocks = sampler.summary()
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * pts * steps * args.steps / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, world)
+    value = whole_job_rate(world, pts, steps, args.steps, ms / 1e3)
 
     # roofline of the dominant kernel (the sweep): algorithmic work per launch /
     # average launch duration over the timed region
@@ -575,12 +591,9 @@ def main():
         for _ in range(args.steps):
             plan.run_host(h_in, h_out, steps)
         el = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(el, world)
         nbytes = h_in.numel() * h_in.element_size()
-        e2e = {"value": world * pts * steps * args.steps / el / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_rate(world, pts, steps, args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "api": "stencil_run_host (pinned host buffers)"}
         del h_in, h_out
