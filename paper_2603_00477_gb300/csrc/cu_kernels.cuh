@@ -11,12 +11,15 @@
 // buffers); sub-step s computes the region grown by (t - s) r.  Points that
 // are not interior (the fixed halo, or outside the stored array) keep their
 // value, which re-imposes the Dirichlet boundary after every sub-step.  The
-// last sub-step writes straight to global memory.  Each thread computes a
-// strip of V outputs along the slowest tile axis and reuses every loaded
-// input row/plane across the strip from registers.
+// last sub-step writes straight to global memory.  FP64 (and 3-D): each
+// thread computes a strip of V outputs along the slowest tile axis and reuses
+// every loaded input row/plane across the strip from registers.  FP32 2-D:
+// each thread walks a strip of rows for four adjacent columns and rotates
+// the partial sums of the 2r+1 output rows an input row touches through
+// registers (f32_substep4).
 //
-// Weights are kernel parameters (constant bank), K values in the library's
-// lexicographic offset order.
+// Weights are kernel parameters (constant bank; FP64 kernels copy them to
+// shared memory), K values in the library's lexicographic offset order.
 #pragma once
 
 #include <cstdint>

@@ -9,8 +9,11 @@
 // dispatcher also uses to report S.
 //
 // CTA: 256 threads, tile 128 output rows x 64 output columns, persistent over
-// tiles; the next tile's input is copied (cp.async) while this one computes,
-// and B fragments are rounded to TF32 in registers after each load.  Warp w owns the 16-column strip w mod 4 and the 64-row band w / 4.
+// tiles; the next tile's input is copied (cp.async: 16-byte copies when the
+// stored rows are 16-byte multiples, the tile grid then shifted so each
+// window starts on a 16-byte boundary) while this one computes, where two
+// staging buffers fit; every thread rounds the elements it copied to TF32 in
+// place.  Warp w owns the 16-column strip w mod 4 and the 64-row band w / 4.
 // Its eight accumulators cover the rows y0 + 8n (y0 = 0..7, n = 0..7) of the
 // band, so the B fragment of input row offset rho = y0 + a (line a) is shared
 // by every (y0, a) with the same sum: a B fragment (one 16-byte shared-memory

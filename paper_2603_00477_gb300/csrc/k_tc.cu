@@ -1,19 +1,22 @@
 // k_tc.cu -- tensor-core sweeps: the t-step composite stencil (kernel fusion,
 // paper Sec. 2.2.3, Eq. 3) run as banded Toeplitz GEMM tiles.
 //
-// FP32 grids (tc2d_sweep): tcgen05.mma with D in TMEM.  A CTA owns 128
-// output rows x 8*NACC output columns; the MMA M axis runs over the 128
-// rows, N = 8 output columns per accumulator, K over the input window.  The
-// input tile sits in shared memory "chunk-column major": 16-byte chunks of
-// consecutive x, with the 16-byte chunks of consecutive rows adjacent.  Any
-// 8 consecutive rows of one chunk column therefore form a canonical K-major
-// core matrix, so the im2col operand A_a of line a is only a descriptor:
-// start = chunk column of the window, row offset a; LBO = one chunk column
-// (HS * 16 bytes), SBO = 8 rows (128 bytes).  No copy is made.  B_a is the
-// Toeplitz block of line a, built in shared memory by the CTA from the
-// composite weights.  One thread issues all MMAs of the tile, commits them to
-// an mbarrier; the four warps then read the accumulators back with
-// tcgen05.ld, stage them through shared memory and store coalesced rows.
+// FP32 grids: tcgen05.mma with D in TMEM.  The MMA M axis runs over 128
+// output rows, N over TN output columns per accumulator, K over the input
+// window.  The input tile sits in shared memory "chunk-column major": 16-byte
+// chunks of consecutive x, with the 16-byte chunks of consecutive rows
+// adjacent.  Any 8 consecutive rows of one chunk column therefore form a
+// canonical K-major core matrix, so the im2col operand A_a of line a is only
+// a descriptor: start = chunk column of the window, row offset a; LBO = one
+// chunk column (HS * 16 bytes), SBO = 8 rows (128 bytes).  No copy is made.
+// B_a is the Toeplitz block of line a, built in shared memory by the CTA
+// from the composite weights.
+//   tc2d_ws (TF32, TF32X3): warp-specialised persistent kernel, TN = 32 (or
+//     16 / 8 where the operands would not fit), double-buffered operands and
+//     accumulators (below).
+//   tc2d_sweep (BF16X3, kind::f16): one tile per CTA, TN = 8; one thread
+//     issues all MMAs of the tile and commits them to an mbarrier, the four
+//     warps read the accumulators back with tcgen05.ld and store rows.
 //
 // Precision forms: TF32 (one product of TF32-rounded operands), TF32X3 and
 // BF16X3 (each operand split into hi + lo, three products hi*hi + hi*lo +
@@ -22,7 +25,7 @@
 // FP64 grids (dmma2d_sweep): the same Toeplitz formulation on the FP64 MMA
 // mma.sync.m8n8k4 (M = 8 output rows, N = 8 output columns, K = 4).
 //
-// Both write interior points farther than (t-1) r from the boundary only:
+// All write interior points farther than (t-1) r from the boundary only:
 // nearer points would need the halo re-imposed between the fused steps; the
 // CUDA-core band kernel computes them stepwise.
 #include <cuda_bf16.h>
@@ -283,20 +286,21 @@ __global__ void __launch_bounds__(128) tc2d_sweep(const float *__restrict__ in, 
 }
 
 // ---------------------------------------------------------------------------
-// Warp-specialised TF32 / TF32x3 sweep (persistent CTAs, 160 threads).
+// Warp-specialised TF32 / TF32x3 sweep (persistent CTAs, 288 threads).
 //
 // An MMA of M=128 rows costs a fixed ~47 cycles for any N <= 64 (measured
 // on GB300 for kind::tf32, K=8), so each MMA covers TN = 16 or 32 output
 // columns (the Toeplitz block is TN x 8) rather than 8: four times the work
-// per instruction for a lower sparsity factor S.  Warp 4 only issues MMAs;
-// warps 0-3 load (cp.async straight into the chunk-column A layout,
-// double-buffered), round / split, and drain the accumulators of the
-// previous tile (tcgen05.ld, double-buffered TMEM).  Three mbarriers per
-// buffer pair hand work over: full[b] (operands of buffer b ready, 128
-// arrivals), done[b] (the MMAs reading buffer b and writing accumulator set
-// b completed, tcgen05.commit), free[b] (accumulator set b read, 128
-// arrivals).  Every wait is bounded; a wait that runs out sets the abort flag
-// and every warp leaves its loop.
+// per instruction for a lower sparsity factor S.  Warp 8 only issues MMAs;
+// warps 0-7 load the next tile (cp.async straight into the chunk-column A
+// layout, 16-byte copies when the stored rows allow, double-buffered) and
+// round / split it; warps 0-3 also drain the accumulators of the previous
+// tile (tcgen05.ld, double-buffered TMEM).  Three mbarriers per buffer pair
+// hand work over: full[b] (operands of buffer b ready, 256 arrivals), done[b]
+// (the MMAs reading buffer b and writing accumulator set b completed,
+// tcgen05.commit), free[b] (accumulator set b read, 128 arrivals).  Every
+// wait is bounded; a wait that runs out sets the abort flag and every warp
+// leaves its loop.
 // ---------------------------------------------------------------------------
 template <int PREC, int TN_, int NACC>
 __global__ void __launch_bounds__(288, 1)
