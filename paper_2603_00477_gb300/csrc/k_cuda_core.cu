@@ -1,12 +1,13 @@
-// k_cuda_core.cu -- instantiations and launcher of the CUDA-core sweeps
-// (templates in cu_kernels.cuh).  2-D: box and star, r = 1..7.  3-D: box
-// r = 1..2, star r = 1..4.  FP64 and FP32.
+// k_cuda_core.cu -- dispatch of the CUDA-core sweeps (kernels in
+// cu_kernels.cuh, launchers in k_cuda_core_impl.cuh, instantiated per group
+// in k_cu2d_*.cu and k_cu3d.cu).
+// 2-D: box and star, r = 1..7.  3-D: box r = 1..2, star r = 1..4.  FP64 and
+// FP32.
 #include <algorithm>
 #include <atomic>
 #include <string>
 
-#include "cu_kernels.cuh"
-#include "launch.h"
+#include "k_cuda_core_impl.cuh"
 
 namespace gbs {
 
@@ -24,182 +25,26 @@ stencil_status ensure_smem(const void *func, size_t bytes, int *cached)
     return STENCIL_OK;
 }
 
-namespace {
-
-template <typename T>
-constexpr int kV = sizeof(T) == 8 ? 4 : 8;  // strip height: FP64 needs fewer accumulators
-constexpr size_t kMaxSmem = 227 * 1024;
-
-// Band ring: tiles that contain a point closer than `band` to the interior
-// boundary.  Along y these are the tile rows below ceil(band/BY) and from
-// floor((ny-band)/BY) on (the last tile row may be partial), likewise in x.
-cu::Ring make_ring(int64_t ny, int64_t nx, int BY, int BX, int band)
-{
-    cu::Ring g{};
-    g.nty = (int)((ny + BY - 1) / BY);
-    g.ntx = (int)((nx + BX - 1) / BX);
-    g.band = band;
-    if (band <= 0) return g;
-    const int top = (int)std::min<int64_t>(g.nty, (band + BY - 1) / BY);
-    const int bot = g.nty - (int)(std::max<int64_t>(0, ny - band) / BY);
-    const int left = (int)std::min<int64_t>(g.ntx, (band + BX - 1) / BX);
-    const int right = g.ntx - (int)(std::max<int64_t>(0, nx - band) / BX);
-    g.top_w = top;
-    g.rows_tb = std::min(g.nty, top + bot);
-    g.left_w = left;
-    g.cols_lr = std::min(g.ntx, left + right);
-    return g;
-}
-
-int64_t ring_count(const cu::Ring &g)
-{
-    if (g.band <= 0) return (int64_t)g.nty * g.ntx;
-    return (int64_t)g.rows_tb * g.ntx + (int64_t)(g.nty - g.rows_tb) * g.cols_lr;
-}
-
-template <typename T, int SHAPE, int R>
-stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
-{
-    using Wt = cu::Weights<T, cu::Taps<SHAPE, 2, R>::K>;
-    static int cached = 0;
-    static int occ_smem = -1, occ_blocks = 0;
-    Wt wt;
-    for (int k = 0; k < cu::Taps<SHAPE, 2, R>::K; k++) wt.w[k] = (T)p.w[k];
-    int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
-    if (band > 0 || p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
-    const int BY = tile[1], BX = tile[2];
-    const size_t H = BY + 2 * t * R, W = BX + 2 * t * R;
-    const size_t bufb = cu::buf_elems<T>((int)H, (int)W) * sizeof(T);
-    // weights (FP64) + two staging buffers (+ a work buffer for t > 1)
-    const size_t smem = cu::weight_smem_bytes<T, cu::Taps<SHAPE, 2, R>::K>() + bufb * (t > 1 ? 3 : 2);
-    if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
-    auto kern = cu::cu2d_sweep<T, SHAPE, R, kV<T>>;
-    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
-    if (s != STENCIL_OK) return s;
-    if (occ_smem != (int)smem) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        occ_smem = (int)smem;
-    }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cu::Ring ring = make_ring(p.dims[1], p.dims[2], BY, BX, band);
-    if (sizeof(T) == 4 && band == 0 && p.ext[2] % 4 == 0 && BX % 4 == 0 &&
-        reinterpret_cast<uintptr_t>(in) % 16 == 0) {
-        // shift the tile grid left so that each staged window starts on a
-        // 16-byte boundary (window start = R + bx BX - t R - xshift)
-        ring.xshift = (int)(((int64_t)R * (1 - t) % 4 + 4) % 4);
-        ring.vec16 = 1;
-        ring.ntx = (int)((p.dims[2] + ring.xshift + BX - 1) / BX);
-    }
-    const int64_t ntiles = ring_count(ring);
-    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
-    const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, resident);
-    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[1], p.ext[2], BY, BX, t, ring,
-                                           (int)ntiles);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu2d_sweep launch");
-}
-
-template <typename T, int SHAPE, int R>
-stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
-{
-    using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
-    static int cached = 0;
-    static int occ_smem = -1, occ_blocks = 0;
-    Wt wt;
-    for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];
-    int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
-    if (p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
-    const int BZ = tile[0], BY = tile[1], BX = tile[2];
-    const size_t Z = BZ + 2 * t * R, H = BY + 2 * t * R, W = BX + 2 * t * R;
-    const size_t smem =
-        cu::weight_smem_bytes<T, cu::Taps<SHAPE, 3, R>::K>() + Z * H * W * sizeof(T) * (t > 1 ? 3 : 2);
-    if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
-    auto kern = cu::cu3d_sweep<T, SHAPE, R, kV<T>>;
-    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
-    if (s != STENCIL_OK) return s;
-    if (occ_smem != (int)smem) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        occ_smem = (int)smem;
-    }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t nz = p.dims[0], ny = p.dims[1], nx = p.dims[2];
-    const int64_t tx = (nx + BX - 1) / BX, ty = (ny + BY - 1) / BY, tz = (nz + BZ - 1) / BZ;
-    const int64_t ntiles = tx * ty * tz;
-    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
-    const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, resident);
-    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[0], p.ext[1], p.ext[2], BZ, BY, BX,
-                                           t, (int)tx, (int)ty, (int)ntiles);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu3d_sweep launch");
-}
-
-template <typename T>
-stencil_status launch_typed(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
-{
-    const int shape = p.pat.shape, r = p.pat.r;
-    if (p.pat.d == 2) {
-        if (shape == STENCIL_BOX) {
-            switch (r) {
-            case 1: return launch2d<T, 0, 1>(p, in, out, t, band, st);
-            case 2: return launch2d<T, 0, 2>(p, in, out, t, band, st);
-            case 3: return launch2d<T, 0, 3>(p, in, out, t, band, st);
-            case 4: return launch2d<T, 0, 4>(p, in, out, t, band, st);
-            case 5: return launch2d<T, 0, 5>(p, in, out, t, band, st);
-            case 6: return launch2d<T, 0, 6>(p, in, out, t, band, st);
-            case 7: return launch2d<T, 0, 7>(p, in, out, t, band, st);
-            }
-        } else {
-            switch (r) {
-            case 1: return launch2d<T, 1, 1>(p, in, out, t, band, st);
-            case 2: return launch2d<T, 1, 2>(p, in, out, t, band, st);
-            case 3: return launch2d<T, 1, 3>(p, in, out, t, band, st);
-            case 4: return launch2d<T, 1, 4>(p, in, out, t, band, st);
-            case 5: return launch2d<T, 1, 5>(p, in, out, t, band, st);
-            case 6: return launch2d<T, 1, 6>(p, in, out, t, band, st);
-            case 7: return launch2d<T, 1, 7>(p, in, out, t, band, st);
-            }
-        }
-    } else {
-        if (shape == STENCIL_BOX) {
-            switch (r) {
-            case 1: return launch3d<T, 0, 1>(p, in, out, t, st);
-            case 2: return launch3d<T, 0, 2>(p, in, out, t, st);
-            }
-        } else {
-            switch (r) {
-            case 1: return launch3d<T, 1, 1>(p, in, out, t, st);
-            case 2: return launch3d<T, 1, 2>(p, in, out, t, st);
-            case 3: return launch3d<T, 1, 3>(p, in, out, t, st);
-            case 4: return launch3d<T, 1, 4>(p, in, out, t, st);
-            }
-        }
-    }
-    return fail(STENCIL_ERR_UNSUPPORTED, "no CUDA-core kernel for this (shape, d, r)");
-}
-
-}  // namespace
-
 stencil_status launch_cu_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
-    if (p.dtype == STENCIL_F64) return launch_typed<double>(p, in, out, t, 0, st);
-    return launch_typed<float>(p, in, out, t, 0, st);
+    if (p.pat.d == 3) return launch_cu3d(p, in, out, t, st);
+    if (p.pat.d != 2) return fail(STENCIL_ERR_UNSUPPORTED, "no CUDA-core kernel for this d");
+    return launch_cu_band(p, in, out, t, 0, st);
 }
 
 stencil_status launch_cu_band(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
 {
     if (p.pat.d != 2) return fail(STENCIL_ERR_UNSUPPORTED, "band sweep: 2-D only");
-    if (p.dtype == STENCIL_F64) return launch_typed<double>(p, in, out, t, band, st);
-    return launch_typed<float>(p, in, out, t, band, st);
+    if (p.dtype == STENCIL_F64) return launch_cu2d_f64(p, in, out, t, band, st);
+    const int r = p.pat.r;
+    if (p.pat.shape == STENCIL_BOX) {
+        if (r <= 3) return launch_cu2d_f32_box_r13(p, in, out, t, band, st);
+        if (r <= 5) return launch_cu2d_f32_box_r45(p, in, out, t, band, st);
+        if (r == 6) return launch_cu2d_f32_box_r6(p, in, out, t, band, st);
+        return launch_cu2d_f32_box_r7(p, in, out, t, band, st);
+    }
+    if (r <= 4) return launch_cu2d_f32_star_r14(p, in, out, t, band, st);
+    return launch_cu2d_f32_star_r57(p, in, out, t, band, st);
 }
 
 }  // namespace gbs

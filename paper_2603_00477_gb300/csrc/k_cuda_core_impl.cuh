@@ -1,0 +1,158 @@
+// k_cuda_core_impl.cuh -- host launchers of the CUDA-core sweeps
+// (templates; instantiated in k_cu2d_*.cu and k_cu3d.cu so that the
+// instantiations compile in parallel).
+#pragma once
+
+#include <algorithm>
+#include <string>
+
+#include "cu_kernels.cuh"
+#include "launch.h"
+
+namespace gbs {
+namespace cuimpl {
+
+
+template <typename T>
+constexpr int kV = sizeof(T) == 8 ? 4 : 8;  // strip height: FP64 needs fewer accumulators
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// Band ring: tiles that contain a point closer than `band` to the interior
+// boundary.  Along y these are the tile rows below ceil(band/BY) and from
+// floor((ny-band)/BY) on (the last tile row may be partial), likewise in x.
+inline cu::Ring make_ring(int64_t ny, int64_t nx, int BY, int BX, int band)
+{
+    cu::Ring g{};
+    g.nty = (int)((ny + BY - 1) / BY);
+    g.ntx = (int)((nx + BX - 1) / BX);
+    g.band = band;
+    if (band <= 0) return g;
+    const int top = (int)std::min<int64_t>(g.nty, (band + BY - 1) / BY);
+    const int bot = g.nty - (int)(std::max<int64_t>(0, ny - band) / BY);
+    const int left = (int)std::min<int64_t>(g.ntx, (band + BX - 1) / BX);
+    const int right = g.ntx - (int)(std::max<int64_t>(0, nx - band) / BX);
+    g.top_w = top;
+    g.rows_tb = std::min(g.nty, top + bot);
+    g.left_w = left;
+    g.cols_lr = std::min(g.ntx, left + right);
+    return g;
+}
+
+inline int64_t ring_count(const cu::Ring &g)
+{
+    if (g.band <= 0) return (int64_t)g.nty * g.ntx;
+    return (int64_t)g.rows_tb * g.ntx + (int64_t)(g.nty - g.rows_tb) * g.cols_lr;
+}
+
+template <typename T, int SHAPE, int R>
+stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
+{
+    using Wt = cu::Weights<T, cu::Taps<SHAPE, 2, R>::K>;
+    static int cached = 0;
+    static int occ_smem = -1, occ_blocks = 0;
+    Wt wt;
+    for (int k = 0; k < cu::Taps<SHAPE, 2, R>::K; k++) wt.w[k] = (T)p.w[k];
+    int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
+    if (band > 0 || p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
+    const int BY = tile[1], BX = tile[2];
+    const size_t H = BY + 2 * t * R, W = BX + 2 * t * R;
+    const size_t bufb = cu::buf_elems<T>((int)H, (int)W) * sizeof(T);
+    // weights (FP64) + two staging buffers (+ a work buffer for t > 1)
+    const size_t smem = cu::weight_smem_bytes<T, cu::Taps<SHAPE, 2, R>::K>() + bufb * (t > 1 ? 3 : 2);
+    if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
+    auto kern = cu::cu2d_sweep<T, SHAPE, R, kV<T>>;
+    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    if (s != STENCIL_OK) return s;
+    if (occ_smem != (int)smem) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        occ_smem = (int)smem;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cu::Ring ring = make_ring(p.dims[1], p.dims[2], BY, BX, band);
+    if (sizeof(T) == 4 && band == 0 && p.ext[2] % 4 == 0 && BX % 4 == 0 &&
+        reinterpret_cast<uintptr_t>(in) % 16 == 0) {
+        // shift the tile grid left so that each staged window starts on a
+        // 16-byte boundary (window start = R + bx BX - t R - xshift)
+        ring.xshift = (int)(((int64_t)R * (1 - t) % 4 + 4) % 4);
+        ring.vec16 = 1;
+        ring.ntx = (int)((p.dims[2] + ring.xshift + BX - 1) / BX);
+    }
+    const int64_t ntiles = ring_count(ring);
+    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, resident);
+    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[1], p.ext[2], BY, BX, t, ring,
+                                           (int)ntiles);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu2d_sweep launch");
+}
+
+template <typename T, int SHAPE, int R>
+stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
+{
+    using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
+    static int cached = 0;
+    static int occ_smem = -1, occ_blocks = 0;
+    Wt wt;
+    for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];
+    int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
+    if (p.path != STENCIL_PATH_CUDA_CORE) cu_default_tile(p, t, tile);
+    const int BZ = tile[0], BY = tile[1], BX = tile[2];
+    const size_t Z = BZ + 2 * t * R, H = BY + 2 * t * R, W = BX + 2 * t * R;
+    const size_t smem =
+        cu::weight_smem_bytes<T, cu::Taps<SHAPE, 3, R>::K>() + Z * H * W * sizeof(T) * (t > 1 ? 3 : 2);
+    if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
+    auto kern = cu::cu3d_sweep<T, SHAPE, R, kV<T>>;
+    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    if (s != STENCIL_OK) return s;
+    if (occ_smem != (int)smem) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        occ_smem = (int)smem;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t nz = p.dims[0], ny = p.dims[1], nx = p.dims[2];
+    const int64_t tx = (nx + BX - 1) / BX, ty = (ny + BY - 1) / BY, tz = (nz + BZ - 1) / BZ;
+    const int64_t ntiles = tx * ty * tz;
+    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const int64_t resident = (int64_t)std::max(1, occ_blocks) * std::max(1, sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, resident);
+    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[0], p.ext[1], p.ext[2], BZ, BY, BX,
+                                           t, (int)tx, (int)ty, (int)ntiles);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu3d_sweep launch");
+}
+
+
+// Launcher of one (dtype, shape) group for the radii RLO..RHI.
+template <typename T, int SHAPE, int RLO, int RHI>
+stencil_status launch2d_range(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
+{
+    if constexpr (RLO <= RHI) {
+        if (p.pat.r == RLO) return launch2d<T, SHAPE, RLO>(p, in, out, t, band, st);
+        return launch2d_range<T, SHAPE, RLO + 1, RHI>(p, in, out, t, band, st);
+    }
+    return fail(STENCIL_ERR_UNSUPPORTED, "no CUDA-core kernel for this (shape, d, r)");
+}
+
+}  // namespace cuimpl
+
+// One translation unit each (the large FP32 radii compile longest, so they
+// are split by radius).
+stencil_status launch_cu2d_f32_box_r13(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu2d_f32_box_r45(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu2d_f32_box_r6(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu2d_f32_box_r7(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu2d_f32_star_r14(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu2d_f32_star_r57(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu2d_f64(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st);
+stencil_status launch_cu3d(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
+
+}  // namespace gbs
