@@ -380,6 +380,8 @@ stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *i
                                       int64_t steps, int reps, stencil_stream_t stream,
                                       stencil_batch_tune_result *results, int max_results, int *n_results);
 
+/* Release a batch and its cached graph (never frees caller workspace).  Null
+ * is ignored. */
 void stencil_batch_destroy(stencil_batch *batch);
 
 /* ---- model ------------------------------------------------------------- */
