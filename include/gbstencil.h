@@ -412,8 +412,13 @@ stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_stream_t str
  * affected outputs were not written).  Clears the flag. */
 stencil_status stencil_device_status(stencil_stream_t stream);
 
+/* Static name of a status code ("STENCIL_OK", ...); never null. */
 const char *stencil_status_string(stencil_status s);
+
+/* Message of the last failing call on the calling thread (thread-local,
+ * valid until that thread's next failing call); "" if none. */
 const char *stencil_last_error(void);
+
 /* Kernel launches issued through this library since it was loaded, by all
  * threads (counted on the host at each launch). */
 uint64_t stencil_launch_count(void);
