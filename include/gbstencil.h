@@ -412,7 +412,8 @@ stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_stream_t str
  * affected outputs were not written).  Clears the flag. */
 stencil_status stencil_device_status(stencil_stream_t stream);
 
-/* Static name of a status code ("STENCIL_OK", ...); never null. */
+/* Static description of a status code ("ok", "invalid argument", ...;
+ * "unknown status" for other values); never null. */
 const char *stencil_status_string(stencil_status s);
 
 /* Message of the last failing call on the calling thread (thread-local,
