@@ -8,7 +8,8 @@
  * tiles), and picks the path and t with the performance model of
  * arxiv 2603.00477 ("Do We Need Tensor Cores for Stencil Computations?").
  *
- * What one step computes (paper Sec. 1, the stencil definition): every
+ * What one step computes (paper Sec. 1 and Sec. 3.2.1, the original
+ * stencil problem: one FMA per neighbouring point): every
  * interior point p of the grid becomes
  *       u_{n+1}[p] = sum_{o in O} w_o * u_n[p + o],
  * where O is the box [-r, r]^d or the star (offsets with at most one non-zero
@@ -156,7 +157,10 @@ typedef struct stencil_plan stencil_plan;
 
 /* ---- plans ------------------------------------------------------------- */
 
-/* Create a plan for `shape` (d in {2,3}, r >= 1) with K weights (copied;
+/* Create a plan for the stencil of Sec. 3.2.1 (K = (2r+1)^d box points or
+ * 2dr+1 star points), fused t steps at a time (Sec. 3.2.2 temporal fusion on
+ * CUDA cores, Sec. 2.2.3 kernel fusion on tensor cores), path and t chosen
+ * by the model of Secs. 3-4 (Eqs. 8-20): `shape` (d in {2,3}, r >= 1), K weights (copied;
  * lexicographic offset order), element type `dtype`, interior extents
  * dims[0..d-1] (slowest first, each >= 1) and fusion depth t (0 = let the
  * model choose, else 1..16).  Host only: no CUDA call, no device memory.
@@ -166,7 +170,9 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
                                    const double *weights, stencil_dtype dtype,
                                    const int64_t *dims, int t);
 
-/* Set an option and re-run dispatch.  Keys and values:
+/* Set an option and re-run dispatch (paths: Sec. 3.2.2 CUDA cores, Sec.
+ * 3.2.3 tensor cores, Sec. 4.3 sparse tensor cores; the split-precision forms
+ * have no counterpart in the paper).  Keys and values:
  *   "path"      auto | cuda_core | tensor_core | sparse_tensor_core
  *   "precision" native | tf32 | tf32x3 | bf16x3 | any
  *   "t"         0 (model) or 1..16
@@ -178,7 +184,8 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
  * path/precision has no kernel for this plan (the plan is then unchanged). */
 stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, const char *value);
 
-/* What dispatch chose, with the model's predictions (host only). */
+/* What dispatch chose, with the model's predictions (host only): alpha
+ * (Eq. 9), S (Sec. 2.2.2), intensity (Eqs. 8, 11), scenario (Sec. 4.1). */
 stencil_status stencil_plan_info(const stencil_plan *plan, stencil_info *info);
 
 /* Bytes of device workspace stencil_run needs: one stored grid, used as
@@ -192,7 +199,9 @@ size_t stencil_plan_workspace_bytes(const stencil_plan *plan, int for_host_io);
  * INVALID_ARG if ptr is null with bytes > 0. */
 stencil_status stencil_plan_set_workspace(stencil_plan *plan, void *dev_ptr, size_t bytes);
 
-/* Run `steps` steps from `in` to `out` (device buffers of the stored size,
+/* The repeated sweeps themselves (Sec. 3.2.1 per step; Sec. 3.2.2 / 2.2.3
+ * per fused sweep).
+ * Run `steps` steps from `in` to `out` (device buffers of the stored size,
  * halo included) on `stream`.  `in` is read only; its halo defines the fixed
  * boundary and is copied to `out`.  steps = 0 copies in to out.  The run is
  * ceil(steps/t) fused sweeps, the last one shorter if t does not divide
@@ -202,14 +211,17 @@ stencil_status stencil_plan_set_workspace(stencil_plan *plan, void *dev_ptr, siz
 stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_t steps,
                            stencil_stream_t stream);
 
-/* Same computation from host memory: copies host_in to the device,
+/* stencil_run from host memory (no counterpart in the paper).
+ * Same computation from host memory: copies host_in to the device,
  * runs, copies the result to host_out, and synchronises `stream` before
  * returning.  Needs stencil_plan_workspace_bytes(plan, 1) of workspace.
  * Pinned host memory gives full copy bandwidth. */
 stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out,
                                 int64_t steps, stencil_stream_t stream);
 
-/* The tensor-core operand layout of this plan's (dtype, precision) at fusion
+/* The zero-padded Toeplitz operands of the tensor-core path (Sec. 2.2.1-2.2.3;
+ * S as in Sec. 2.2.2).
+ * The tensor-core operand layout of this plan's (dtype, precision) at fusion
  * depth t (host only).  kb_lo/kb_hi receive 2R+1 ints each; B (optional)
  * receives the FP64 Toeplitz blocks in [a][kb][k][n] order,
  * (2R+1) * nkb * k_inst * n_tile doubles.  Any of kb_lo, kb_hi, B may be null.
@@ -251,7 +263,8 @@ typedef struct {
     double sparsity; /* S = useful MACs / logical issued MACs */
 } stencil_sptc_layout;
 
-/* The sparse layout of this plan at fusion depth t (host only; FP32 plans,
+/* The 2:4-structured (TF32: 1:2) sparse operands of Sec. 4.3.
+ * The sparse layout of this plan at fusion depth t (host only; FP32 plans,
  * 2-D, t*r <= 12, else UNSUPPORTED).  chunk_first / chunk_second receive
  * 2*ns ints (-1 = a dummy chunk); line_mask receives 2R+1 bytes (bit s: line
  * issues instruction s); values / select receive the compressed A operand,
@@ -270,7 +283,9 @@ typedef struct {
     int tile_y, tile_x;         /* the tile the candidate ran with */
 } stencil_tune_result;
 
-/* Autotuner seeded by the model: runs every (path, precision, t) the plan's
+/* Measurement-based choice among the candidates the model of Secs. 3-4
+ * ranks (the tuner itself has no counterpart in the paper).
+ * Autotuner seeded by the model: runs every (path, precision, t) the plan's
  * options allow, in the model's order (2-D CUDA-core candidates also with the
  * tiles 32x256, 64x128, 64x64, 32x128 and 128x64 unless a tile was set),
  * `reps` times `steps` steps on the
@@ -299,7 +314,9 @@ typedef struct {
 
 typedef struct stencil_batch stencil_batch;
 
-/* Many independent 2-D grids of uneven size and mixed stencils, all of one
+/* The batched form: the sweeps of Sec. 3.2.2 over many grids in one
+ * persistent launch (no counterpart in the paper).
+ * Many independent 2-D grids of uneven size and mixed stencils, all of one
  * dtype, run together: one persistent launch whose CTAs pull (grid, tile,
  * sweep) work items from a device queue; an item of sweep s waits (bounded)
  * for every tile of sweep s-1 of its grid.  Each grid gets the CUDA-core
@@ -364,7 +381,9 @@ typedef struct {
     int chosen;                 /* 1 for the class's winner                    */
 } stencil_batch_tune_result;
 
-/* Autotuner of the batched form, seeded by the model: groups the grids into
+/* Per-shape-class tuning of the batched form, candidates ranked by the model
+ * of Secs. 3-4 (no counterpart in the paper).
+ * Autotuner of the batched form, seeded by the model: groups the grids into
  * shape classes (stencil shape, radius, size class), ranks each class's
  * candidates -- CUDA-core work items (t = 1..4, tiles 16x64 .. 128x128) and,
  * for size classes >= 3 when the batch precision allows (FP64 batches, or
@@ -393,7 +412,9 @@ void stencil_batch_destroy(stencil_batch *batch);
  * non-positive peak or bandwidth. */
 stencil_status stencil_model_predict(const stencil_model_in *in, stencil_model_out *out);
 
-/* Replace the process-wide peak table the dispatcher uses (zero fields
+/* The roofline inputs of Sec. 3.1 (peak compute per unit and bandwidth B;
+ * P_SpTC of Eq. 20).
+ * Replace the process-wide peak table the dispatcher uses (zero fields
  * unchanged) / read it.  Defaults are GB300 figures. */
 stencil_status stencil_set_peaks(const stencil_peaks *peaks);
 stencil_status stencil_get_peaks(stencil_peaks *peaks);
