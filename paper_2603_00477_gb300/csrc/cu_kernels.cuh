@@ -699,5 +699,144 @@ __global__ void __launch_bounds__(kThreads, 2)
     cp_async_wait_group<0>();
 }
 
+// ---------------------------------------------------------------------------
+// 3-D, one step per sweep (t = 1), 2.5-D streaming: a work item is a
+// (BY x BX) tile of one z chunk of CZ planes.  The CTA marches along z with a
+// ring of NP = 2R + 2 input planes (each the tile grown by R in y and x) in
+// shared memory: plane z + R + 1 is copied (cp.async) while plane z is
+// computed, so every input plane is read once per tile and the only
+// re-reads are the y/x halo.  256 threads: thread (ty, tx) = (tid / 16,
+// tid % 16) computes outputs (y, x0 .. x0 + 3) for x0 = 4 tx and the RPT rows
+// y = ty + 16 i; each (oz, oy) row segment of 4 + 2R values is loaded once
+// and used for the 4 outputs.
+// ---------------------------------------------------------------------------
+constexpr int kStreamCZ = 64;
+
+template <typename T>
+__host__ __device__ constexpr int stream_rows_per_thread()
+{
+    return sizeof(T) == 4 ? 2 : 1;  // BY = 16 * RPT: 32 (FP32), 16 (FP64)
+}
+
+template <typename T, int R>
+__host__ __device__ constexpr int stream_pitch()
+{
+    return 64 + 2 * R;  // BX = 64 plus the x halo
+}
+
+template <typename T, int R>
+__host__ __device__ constexpr int stream_plane_elems()
+{
+    return (16 * stream_rows_per_thread<T>() + 2 * R) * stream_pitch<T, R>();
+}
+
+template <typename T, int R>
+__host__ __device__ constexpr size_t stream_smem_bytes(int K)
+{
+    return (sizeof(T) == 8 ? (size_t)((K * sizeof(T) + 15) / 16 * 16) : 0) +
+           (size_t)(2 * R + 2) * stream_plane_elems<T, R>() * sizeof(T);
+}
+
+template <typename T, int SHAPE, int R>
+__global__ void __launch_bounds__(kThreads, 2)
+    cu3d_stream(const T *__restrict__ in, T *__restrict__ out,
+                const __grid_constant__ Weights<T, Taps<SHAPE, 3, R>::K> wt, int64_t Ez, int64_t Ey, int64_t Ex,
+                int tiles_x, int tiles_y, int chunks_z, int nitems)
+{
+    constexpr int KT = Taps<SHAPE, 3, R>::K;
+    constexpr bool kSmemW = sizeof(T) == 8;
+    constexpr int RPT = stream_rows_per_thread<T>(), BY = 16 * RPT, BX = 64;
+    constexpr int PW = stream_pitch<T, R>(), PH = BY + 2 * R, PE = stream_plane_elems<T, R>();
+    constexpr int NP = 2 * R + 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *wsm = reinterpret_cast<T *>(smem_raw);
+    if (kSmemW) {
+        for (int k = threadIdx.x; k < KT; k += blockDim.x) wsm[k] = wt.w[k];
+    }
+    T *ring = reinterpret_cast<T *>(smem_raw + (kSmemW ? (KT * sizeof(T) + 15) / 16 * 16 : 0));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ty = tid >> 4, tx = tid & 15, x0 = 4 * tx;
+    const int64_t nz = Ez - 2 * R, ny = Ey - 2 * R, nx = Ex - 2 * R;
+
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int bx = item % tiles_x, by = (item / tiles_x) % tiles_y, bz = item / (tiles_x * tiles_y);
+        // stored coordinates of the first output of the item
+        const int64_t Z0 = R + (int64_t)bz * kStreamCZ, Y0 = R + (int64_t)by * BY, X0 = R + (int64_t)bx * BX;
+        const int64_t rem = nz - (Z0 - R);
+        const int nzo = (int)(rem < kStreamCZ ? rem : kStreamCZ);  // output planes of this item
+        const int64_t zfirst = Z0 - R;                                // first input plane
+        // copy input plane gz (rows Y0-R.., columns X0-R.., zero outside the
+        // stored grid) into its ring slot
+        auto load_plane = [&](int64_t gz) {
+            T *dst = ring + (size_t)((gz - zfirst) % NP) * PE;
+            const bool zok = gz >= 0 && gz < Ez;
+            for (int row = warp; row < PH; row += kThreads / 32) {
+                const int64_t gy = Y0 - R + row;
+                const bool rok = zok && gy >= 0 && gy < Ey;
+                const T *src = in + ((rok ? gz : 0) * Ey + (rok ? gy : 0)) * Ex;
+                for (int c = lane; c < PW; c += 32) {
+                    const int64_t gx = X0 - R + c;
+                    const bool ok = rok && gx >= 0 && gx < Ex;
+                    cp_async_elem<sizeof(T)>(dst + row * PW + c, ok ? src + gx : in, ok);
+                }
+            }
+        };
+        __syncthreads();  // the previous item's reads of the ring are done
+        for (int k = 0; k < 2 * R + 1; ++k) load_plane(zfirst + k);
+        cp_async_commit();
+        for (int zo = 0; zo < nzo; ++zo) {
+            // planes zo .. zo + 2R (relative to zfirst) are needed; prefetch the next
+            if (zo + 1 < nzo) load_plane(zfirst + zo + 2 * R + 1);
+            cp_async_commit();
+            cp_async_wait_group<1>();  // everything but the newest plane has landed
+            __syncthreads();
+            T acc[RPT][4];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = T(0);
+#pragma unroll
+            for (int oz = -R; oz <= R; ++oz) {
+                const T *pl = ring + (size_t)((zo + R + oz) % NP) * PE;
+#pragma unroll
+                for (int oy = -R; oy <= R; ++oy) {
+                    bool any = false;
+#pragma unroll
+                    for (int ox = -R; ox <= R; ++ox) any = any || tap_index<SHAPE, 3, R>(oz, oy, ox) >= 0;
+                    if (!any) continue;
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i) {
+                        const T *rowp = pl + (ty + 16 * i + R + oy) * PW + x0;
+                        T v[4 + 2 * R];
+#pragma unroll
+                        for (int c = 0; c < 4 + 2 * R; ++c) v[c] = rowp[c];
+#pragma unroll
+                        for (int ox = -R; ox <= R; ++ox) {
+                            const int k = tap_index<SHAPE, 3, R>(oz, oy, ox);
+                            if (k >= 0) {
+                                const T wk = kSmemW ? wsm[k] : wt.w[k];
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) acc[i][c] = fma(wk, v[c + R + ox], acc[i][c]);
+                            }
+                        }
+                    }
+                }
+            }
+            const int64_t gz = Z0 + zo;
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int64_t gy = Y0 + ty + 16 * i;
+                if (gy - R >= ny) continue;
+                T *orow = out + (gz * Ey + gy) * Ex;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int64_t gx = X0 + x0 + c;
+                    if (gx - R < nx) orow[gx] = acc[i][c];
+                }
+            }
+            __syncthreads();  // plane zo is no longer read before its slot is refilled
+        }
+    }
+    cp_async_wait_group<0>();
+}
+
 }  // namespace cu
 }  // namespace gbs

@@ -91,9 +91,45 @@ stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int ban
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu2d_sweep launch");
 }
 
+// 3-D, t = 1: the streaming kernel (tile 16 RPT x 64 in y, x; chunks of
+// kStreamCZ planes in z).
+template <typename T, int SHAPE, int R>
+stencil_status launch3d_stream(const Plan &p, const void *in, void *out, cudaStream_t st)
+{
+    using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
+    static int cached = 0;
+    static int occ = -1;
+    Wt wt;
+    for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];
+    const size_t smem = cu::stream_smem_bytes<T, R>(cu::Taps<SHAPE, 3, R>::K);
+    if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "3-D streaming tile does not fit in shared memory");
+    auto kern = cu::cu3d_stream<T, SHAPE, R>;
+    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    if (s != STENCIL_OK) return s;
+    if (occ < 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cu::kThreads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int BY = 16 * cu::stream_rows_per_thread<T>(), BX = 64;
+    const int64_t tz = (p.dims[0] + cu::kStreamCZ - 1) / cu::kStreamCZ, tyy = (p.dims[1] + BY - 1) / BY,
+                  txx = (p.dims[2] + BX - 1) / BX;
+    const int64_t items = tz * tyy * txx;
+    if (items > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)std::max(1, occ) * std::max(1, sms));
+    kern<<<grid, cu::kThreads, smem, st>>>((const T *)in, (T *)out, wt, p.ext[0], p.ext[1], p.ext[2], (int)txx,
+                                           (int)tyy, (int)tz, (int)items);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu3d_stream launch");
+}
+
 template <typename T, int SHAPE, int R>
 stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
+    if (t == 1) return launch3d_stream<T, SHAPE, R>(p, in, out, st);
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
     static int cached = 0;
     static int occ_smem = -1, occ_blocks = 0;

@@ -40,9 +40,14 @@ bool cu_supported(int shape, int d, int r)
     return false;
 }
 
+// Largest t the dispatcher considers on its own (an explicit t may be larger).
+// 3-D: one step per sweep.  The streaming t = 1 kernel reads each plane once
+// per tile (only the y/x halo is re-read); fused 3-D tiles re-read
+// (T + 2tR)^3 / T^3 of the grid per sweep, which the model's one-read-one-
+// write memory term leaves out (measured on GB300: 2-20x slower than t = 1).
 static int max_fused_t(const Plan &p, int path)
 {
-    if (path == STENCIL_PATH_CUDA_CORE) return p.pat.d == 2 ? 4 : 2;
+    if (path == STENCIL_PATH_CUDA_CORE) return p.pat.d == 2 ? 4 : 1;
     return 4;
 }
 
@@ -67,6 +72,11 @@ void cu_default_tile(const Plan &p, int t, int tile[3])
             if (bytes <= 112 * 1024 || (tile[2] <= 16 && tile[1] <= 16)) break;
             if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
         }
+    } else if (t == 1) {
+        // the streaming kernel: chunks of 64 planes of a (16 RPT) x 64 tile
+        tile[0] = 64;
+        tile[1] = p.dtype == STENCIL_F64 ? 16 : 32;
+        tile[2] = 64;
     } else {
         tile[0] = 8;
         tile[1] = 8;
