@@ -264,3 +264,23 @@ def test_batch_precision_and_path_options(lib):
         assert B.stencil_batch_info(h64, 0)["path"] == B.PATH_TENSOR_CORE
     finally:
         B.stencil_batch_destroy(h64)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shape,r", [("star", 2), ("box", 1)])
+def test_dispatch_3d_keeps_one_step_per_sweep(lib, dtype, shape, r):
+    """3-D: the dispatcher's own choice is t = 1 (the streaming kernel; fused
+    3-D tiles re-read their halo volume); an explicit t is still honoured."""
+    w = _w(shape, 3, r)
+    h = B.stencil_plan_create(shape, 3, r, w, dtype, (512, 512, 512), 0)
+    try:
+        info = B.stencil_plan_info(h)
+        assert info["path"] == B.PATH_CUDA_CORE and info["t"] == 1
+        assert list(info["tile"]) == [64, 16 if dtype == "f64" else 32, 64]
+    finally:
+        B.stencil_plan_destroy(h)
+    h = B.stencil_plan_create(shape, 3, r, w, dtype, (512, 512, 512), 2)
+    try:
+        assert B.stencil_plan_info(h)["t"] == 2
+    finally:
+        B.stencil_plan_destroy(h)
