@@ -296,12 +296,13 @@ size_t batch_item_smem(int by, int bx, int t, int r, size_t es)
 struct Layout {
     size_t grids_off, items_off, w_off, done_off, ctl_off, pp_off, total;
     int nitems, ndone;
+    bool too_many;  // more work items than an int indexes: the run is refused
     std::vector<size_t> pp_of;  // per grid: offset of its ping-pong buffer (or SIZE_MAX)
 };
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int sweeps_of(const Plan &p, int64_t steps) { return (int)(steps / p.t + (steps % p.t ? 1 : 0)); }
+int64_t sweeps_of(const Plan &p, int64_t steps) { return steps / p.t + (steps % p.t ? 1 : 0); }
 
 int64_t ntiles_of(const Plan &p)
 {
@@ -314,13 +315,14 @@ Layout layout_of(const stencil_batch &b, int64_t steps)
     const size_t es = b.dtype == STENCIL_F64 ? 8 : 4;
     int64_t nitems = 0, ndone = 0, nw = 0;
     for (auto &g : b.grids) {
-        const int ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
+        const int64_t ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
         if (g.on_cu()) nitems += ntiles_of(g.plan) * ns;
         ndone += ns;
         nw += g.plan.pat.K;
     }
-    L.nitems = (int)nitems;
-    L.ndone = (int)ndone;
+    L.too_many = nitems > 0x7fffffff || ndone > 0x7fffffff;  // the device tables index with int
+    L.nitems = L.too_many ? 0 : (int)nitems;
+    L.ndone = L.too_many ? 0 : (int)ndone;
     size_t off = 0;
     L.grids_off = off;
     off = align_up(off + sizeof(bt::GridDev) * b.grids.size(), 256);
@@ -334,7 +336,7 @@ Layout layout_of(const stencil_batch &b, int64_t steps)
     off = align_up(off + sizeof(bt::Ctl), 256);
     L.pp_off = off;
     for (auto &g : b.grids) {
-        const int ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
+        const int64_t ns = steps > 0 ? sweeps_of(g.plan, steps) : 0;
         if (ns > 1) {
             L.pp_of.push_back(off);
             off = align_up(off + g.plan.grid_bytes(), 256);
@@ -424,7 +426,7 @@ stencil_status upload_tables(stencil_batch *b, const Layout &L, const void *cons
         g.ex = p.ext[2];
         g.kind = p.pat.shape * 4 + p.pat.r;
         g.t = p.t;
-        g.nsweeps = b->grids[i].on_cu() ? sweeps_of(p, steps) : 0;  // tensor-core grids have no items
+        g.nsweeps = b->grids[i].on_cu() ? (int)sweeps_of(p, steps) : 0;  // tensor-core grids have no items
         g.rem = (int)(steps % p.t);
         g.by = p.tile[1];
         g.bx = p.tile[2];
@@ -461,6 +463,8 @@ stencil_status check_run_args(stencil_batch *b, const void *const *ins, void *co
                                                      ": null or identical in/out");
     }
     *L = layout_of(*b, steps);
+    if (L->too_many)
+        return fail(STENCIL_ERR_UNSUPPORTED, "stencil_batch_run: more than 2^31 - 1 work items; split the batch");
     if (!b->ws || b->ws_bytes < L->total)
         return fail(STENCIL_ERR_OOM, "stencil_batch_run: workspace smaller than stencil_batch_workspace_bytes");
     return STENCIL_OK;
@@ -852,7 +856,7 @@ stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *i
             }
             if (!ok) continue;
             const Layout Ls = layout_of(sub, steps);
-            if (Ls.total > sub.ws_bytes) continue;  // does not fit the caller's workspace
+            if (Ls.too_many || Ls.total > sub.ws_bytes) continue;  // too large for the caller's workspace
             s = upload_tables(&sub, Ls, sin.data(), sout.data(), steps, st);
             if (s == STENCIL_OK) s = launch_batch(&sub, Ls, sin.data(), sout.data(), steps, st, true);
             if (s == STENCIL_OK && cudaEventRecord(e0, st) != cudaSuccess) s = fail(STENCIL_ERR_CUDA, "event");

@@ -284,3 +284,17 @@ def test_dispatch_3d_keeps_one_step_per_sweep(lib, dtype, shape, r):
         assert B.stencil_plan_info(h)["t"] == 2
     finally:
         B.stencil_plan_destroy(h)
+
+
+def test_batch_refuses_more_work_items_than_an_int_indexes(lib):
+    """2^31 steps of a one-tile grid at t = 1 is more (grid, tile, sweep) items
+    than the device tables index: refused before any upload or launch."""
+    h = B.stencil_batch_create([("star", 1, 16, 16, _w("star", 2, 1))], "f32", 1)
+    try:
+        n0 = B.stencil_launch_count()
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_batch_run(h, [4096], [1 << 20], 1 << 31, 0)
+        assert e.value.status == B.STENCIL_ERR_UNSUPPORTED
+        assert B.stencil_launch_count() == n0
+    finally:
+        B.stencil_batch_destroy(h)
