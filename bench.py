@@ -228,6 +228,19 @@ def traffic_record(kernel_key):
 
 
 
+def kernel_name(info: dict, d: int, dtype: str) -> str:
+    """The sweep kernel a plan launches, from its path, precision and t."""
+    if info["path"] == 1:
+        if d == 2:
+            return "cu2d_sweep"
+        return "cu3d_stream" if info["t"] == 1 else "cu3d_sweep"
+    if info["path"] == 3:
+        return "sptc2d_sweep"
+    if dtype == "f64":
+        return "dmma2d_sweep"
+    return "tc2d_sweep" if info["precision_name"] == "bf16x3" else "tc2d_ws"
+
+
 def max_over_ranks(x: float, world: int) -> float:
     """The largest per-rank value (a duration): every rank gets the maximum.
     Uses a CUDA tensor under NCCL and a CPU tensor under gloo."""
@@ -260,6 +273,76 @@ def _time_runs(fn, stream, reps=3, warm=1):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / 1e3 / reps
+
+
+# The stencils of the paper's problem classification (2-D and 3-D, radius 1 and
+# 2) plus the radii its benchmarks use (3 and 7 in 2-D), box and star.
+CLASSIFY_STENCILS = [(s, 2, r) for s in ("box", "star") for r in (1, 2, 3, 7)] + \
+                    [(s, 3, r) for s in ("box", "star") for r in (1, 2)]
+# The paper's six representative cases (Sec. 5: stencil, t, element type,
+# tensor-core form), re-evaluated with this engine's tiles.
+PAPER_CASES = [("box", 2, 1, 3, "f64", "tensor_core", None), ("box", 2, 3, 1, "f64", "tensor_core", None),
+               ("box", 2, 1, 7, "f32", "sparse_tensor_core", "tf32"),
+               ("box", 2, 7, 1, "f32", "sparse_tensor_core", "tf32"),
+               ("box", 3, 1, 3, "f64", "tensor_core", None), ("box", 3, 1, 7, "f32", "sparse_tensor_core", "tf32")]
+
+
+def _stencil_name(shape, d, r):
+    return f"{shape.capitalize()}-{d}D{r}R"
+
+
+def model_leg(B, inputs, tmax=8):
+    """The model of Secs. 3-4 evaluated on this GPU's peaks, host only.
+
+    classification: for FP32 and FP64 and every stencil of CLASSIFY_STENCILS,
+    the CUDA-core intensity I^(t) of Eq. 8 for t = 1..tmax against the FP
+    pipe's ridge point, and the first t at which the stencil becomes compute
+    bound (the paper's problem-classification figure, which shows FP32 on an
+    A100).  cases: the paper's six representative cases with the CUDA-core
+    plan and the tensor-core plan this engine would run (its alpha, its tiles'
+    S, Eq. 12 intensity, ridge, scenario and predicted rates); null where no
+    tensor-core kernel covers the case (3-D)."""
+    peaks = B.stencil_get_peaks()
+    out = {"peaks": peaks, "tmax": tmax, "classification": {}, "cases": []}
+    for dtype, D, P in (("f32", 4, peaks["cu_f32_flops"]), ("f64", 8, peaks["cu_f64_flops"])):
+        rows = []
+        for shape, d, r in CLASSIFY_STENCILS:
+            I, bound = [], []
+            for t in range(1, tmax + 1):
+                m = B.stencil_model_predict(shape, d, r, t, D, 1.0, 1.0, P, P, peaks["hbm_bytes_per_s"])
+                I.append(m["I_cu"])
+                bound.append("compute" if m["I_cu"] >= m["ridge_cu"] else "memory")
+            first = next((t for t, b in enumerate(bound, 1) if b == "compute"), None)
+            rows.append({"stencil": _stencil_name(shape, d, r), "I": I, "bound": bound,
+                         "ridge": P / peaks["hbm_bytes_per_s"], "compute_bound_from_t": first})
+        out["classification"][dtype] = rows
+    keys = ("t", "alpha", "sparsity", "beta", "intensity", "ridge", "scenario", "memory_bound",
+            "predicted_gstencils", "path_name", "precision_name")
+    for shape, d, r, t, dtype, tc_path, prec in PAPER_CASES:
+        dims = (10240, 10240) if d == 2 else (1024, 1024, 1024)
+        w = inputs.weights(shape, d, r, 1)
+        case = {"stencil": _stencil_name(shape, d, r), "t": t, "dtype": dtype, "dims": list(dims)}
+        cu = B.Plan(shape, d, r, w, dtype, dims, t)
+        cu.set_option("path", "cuda_core")
+        ci = cu.info()
+        case["cuda_core"] = {k: ci[k] for k in keys}
+        case["cuda_core"]["roof_gstencils"] = ci["predicted_cu_gstencils"]
+        cu.close()
+        try:
+            tc = B.Plan(shape, d, r, w, dtype, dims, t)
+            if prec:
+                tc.set_option("precision", prec)
+            tc.set_option("path", tc_path)
+            ti = tc.info()
+            case["tensor_core"] = {k: ti[k] for k in keys}
+            case["scenario"] = ti["scenario"]
+            tc.close()
+        except B.StencilError as e:
+            case["tensor_core"] = None
+            case["tensor_core_unavailable"] = str(e)
+            case["scenario"] = ci["scenario"]
+        out["cases"].append(case)
+    return out
 
 
 def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
@@ -456,8 +539,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and batched legs")
     ap.add_argument("--dims", default=None, help="override the interior extents (profiling), e.g. 6144,6144")
     ap.add_argument("--run-steps", type=int, default=None, help="override the steps per run (profiling)")
-    ap.add_argument("--leg", default="main", choices=["main", "mixed", "batched"],
-                    help="profiling: run only the mixed-precision or the batched leg and print its JSON")
+    ap.add_argument("--leg", default="main", choices=["main", "mixed", "batched", "model"],
+                    help="run only the mixed-precision or the batched leg, or the host-only model "
+                         "classification, and print its JSON")
     ap.add_argument("--batch-grids", type=int, default=512, help="batched leg: the first N grids (profiling)")
     args = ap.parse_args()
 
@@ -471,6 +555,17 @@ def main():
         cfg["steps"] = args.run_steps
     if args.impl == "reference":
         return run_reference(args, cfg, args.config, rank)
+    if args.leg == "model":  # host arithmetic only: no GPU needed
+        from paper_2603_00477_gb300 import binding as B
+        from paper_2603_00477_gb300 import build as gbuild
+        from paper_2603_00477_gb300 import inputs
+        gbuild.build()
+        peaks, peaks_src = measured_peaks()
+        B.stencil_set_peaks(hbm_bytes_per_s=float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) * 1e9)
+        if rank == 0:
+            print(json.dumps({"leg": "model", "peaks_source": f"hbm_gbs of {peaks_src} peaks",
+                              **model_leg(B, inputs)}))
+        return 0
 
     import numpy as np
     import torch
@@ -553,7 +648,7 @@ def main():
     avg_launch_s = ms / 1e3 / sweep_launches
     K = info["K"]
     D = 8 if cfg["dtype"] == "f64" else 4
-    kernel = {1: "cu2d_sweep" if cfg["d"] == 2 else "cu3d_sweep", 3: "sptc2d_sweep"}.get(info["path"], "tc_sweep")
+    kernel = kernel_name(info, cfg["d"], cfg["dtype"])
     kernel_key = f"{kernel}:{args.config}:{info['path_name']}:t{t}"
     traffic = traffic_record(kernel_key)
     if info["memory_bound"]:
