@@ -24,7 +24,10 @@
  * element type double (STENCIL_F64) or float (STENCIL_F32).
  *
  * Conventions for every call:
- *   - No exception crosses this boundary; every call returns a status.
+ *   - No exception crosses this boundary; every call returns a status (an
+ *     unexpected C++ exception inside the library is caught at the entry
+ *     point: a failed host allocation returns STENCIL_ERR_OOM, anything
+ *     else STENCIL_ERR_INTERNAL).
  *   - Device pointers are CUDA device memory of the current device
  *     (allocated by the caller, e.g. through PyTorch), never freed here.
  *   - `stream` is a cudaStream_t (0 = legacy default stream).  Kernels are
@@ -52,8 +55,11 @@ typedef enum {
     STENCIL_ERR_INVALID_ARG = 1, /* a bad argument; nothing was launched */
     STENCIL_ERR_UNSUPPORTED = 2, /* valid, but no kernel for this case   */
     STENCIL_ERR_CUDA = 3,        /* a CUDA call or launch failed          */
-    STENCIL_ERR_OOM = 4,         /* workspace missing or too small        */
-    STENCIL_ERR_TIMEOUT = 5      /* a bounded device wait ran out         */
+    STENCIL_ERR_OOM = 4,         /* workspace missing or too small, or a
+                                    host allocation failed                */
+    STENCIL_ERR_TIMEOUT = 5,     /* a bounded device wait ran out         */
+    STENCIL_ERR_INTERNAL = 6     /* an unexpected host-side exception was
+                                    caught at the entry point             */
 } stencil_status;
 
 typedef enum { STENCIL_BOX = 0, STENCIL_STAR = 1 } stencil_shape;
@@ -180,6 +186,9 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
  *   "debug_unmet_wait"  0 | 1: test hook; 1 makes every tensor-core CTA first
  *               wait ~2 ms on an mbarrier phase that never completes, take the
  *               timeout path (error word set, tile not written) and return
+ *   "debug_host_exception"  bad_alloc | runtime: test hook; the call throws
+ *               that C++ exception inside the library, which the entry point
+ *               turns into STENCIL_ERR_OOM / STENCIL_ERR_INTERNAL
  * INVALID_ARG for an unknown key or value, UNSUPPORTED if the requested
  * path/precision has no kernel for this plan (the plan is then unchanged). */
 stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, const char *value);

@@ -17,7 +17,7 @@ from . import build as _build
 _LIB = None
 
 STENCIL_OK, STENCIL_ERR_INVALID_ARG, STENCIL_ERR_UNSUPPORTED, STENCIL_ERR_CUDA, STENCIL_ERR_OOM, \
-    STENCIL_ERR_TIMEOUT = range(6)
+    STENCIL_ERR_TIMEOUT, STENCIL_ERR_INTERNAL = range(7)
 BOX, STAR = 0, 1
 F64, F32 = 0, 1
 PATH_AUTO, PATH_CUDA_CORE, PATH_TENSOR_CORE, PATH_SPARSE_TENSOR_CORE = range(4)

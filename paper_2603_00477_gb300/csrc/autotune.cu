@@ -23,7 +23,7 @@ stencil_status dispatch_candidates(Plan *p, std::vector<int> *paths, std::vector
 extern "C" stencil_status stencil_plan_autotune(stencil_plan *plan, const void *in, void *out, int64_t steps, int reps,
                                                 stencil_stream_t stream, stencil_tune_result *results, int max_results,
                                                 int *n_results)
-{
+try {
     if (!plan || !in || !out || steps < 1 || reps < 1)
         return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_autotune: bad argument");
     Plan &p = plan->p;
@@ -138,4 +138,6 @@ extern "C" stencil_status stencil_plan_autotune(stencil_plan *plan, const void *
     }
     p = chosen;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_autotune");
 }

@@ -94,6 +94,10 @@ bool tc_supported(const Plan &p, int precision, int path);
 
 // ---- errors ----
 stencil_status fail(stencil_status s, const std::string &msg);
+// Status for a C++ exception caught at ABI entry point `entry` (call from
+// inside the handler): std::bad_alloc / std::length_error -> OOM, anything
+// else -> INTERNAL; records the message without allocating if it cannot.
+stencil_status abi_exception(const char *entry) noexcept;
 void note_launch(uint64_t n = 1);
 
 }  // namespace gbs

@@ -505,7 +505,7 @@ extern "C" {
 
 stencil_status stencil_batch_create(stencil_batch **batch, int n, const stencil_grid_desc *grids, stencil_dtype dtype,
                                     int t)
-{
+try {
     if (!batch) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_create: batch is null");
     *batch = nullptr;
     if (n < 1 || !grids) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_create: need n >= 1 grids");
@@ -539,36 +539,45 @@ stencil_status stencil_batch_create(stencil_batch **batch, int n, const stencil_
     }
     *batch = b;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_create");
 }
 
 size_t stencil_batch_workspace_bytes(const stencil_batch *batch, int64_t steps)
-{
+try {
     if (!batch || steps < 0) return 0;
     return layout_of(*batch, steps).total;
+} catch (...) {
+    gbs::abi_exception("stencil_batch_workspace_bytes");
+    return 0;
 }
 
 stencil_status stencil_batch_set_workspace(stencil_batch *batch, void *dev_ptr, size_t bytes)
-{
+try {
     if (!batch) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_workspace: batch is null");
     if (!dev_ptr && bytes) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_workspace: null with bytes > 0");
     if (dev_ptr != batch->ws) drop_graph(batch->cache);
     batch->ws = dev_ptr;
     batch->ws_bytes = dev_ptr ? bytes : 0;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_set_workspace");
 }
 
 stencil_status stencil_batch_info(const stencil_batch *batch, int i, stencil_info *info)
-{
+try {
     if (!batch || !info || i < 0 || i >= (int)batch->grids.size())
         return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_info: bad argument");
     *info = batch->grids[i].plan.info;
     for (int k = 0; k < 3; k++) info->tile[k] = batch->grids[i].plan.tile[k];
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_info");
 }
 
 stencil_status stencil_batch_run(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
                                  stencil_stream_t stream)
-{
+try {
     Layout L;
     stencil_status s = check_run_args(batch, ins, outs, steps, &L);
     if (s != STENCIL_OK) return s;
@@ -585,11 +594,13 @@ stencil_status stencil_batch_run(stencil_batch *batch, const void *const *ins, v
     s = upload_tables(batch, L, ins, outs, steps, st);
     if (s != STENCIL_OK) return s;
     return launch_batch(batch, L, ins, outs, steps, st, true);
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_run");
 }
 
 stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
                                        stencil_stream_t stream)
-{
+try {
     Layout L;
     stencil_status s = check_run_args(batch, ins, outs, steps, &L);
     if (s != STENCIL_OK) return s;
@@ -641,10 +652,12 @@ stencil_status stencil_batch_run_graph(stencil_batch *batch, const void *const *
     if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_run_graph: launch");
     note_launch(c.kernel_nodes);
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_run_graph");
 }
 
 stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t stream)
-{
+try {
     if (!batch) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_status: batch is null");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_status: stream");
@@ -654,10 +667,12 @@ stencil_status stencil_batch_status(stencil_batch *batch, stencil_stream_t strea
     if (e != cudaSuccess) return cuda_fail(e, "stencil_batch_status: reading the control word");
     if (ctl.abort) return fail(STENCIL_ERR_TIMEOUT, "stencil_batch: a dependency wait ran out; outputs incomplete");
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_status");
 }
 
 stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, const char *value)
-{
+try {
     if (!batch || !key || !value) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_set_option: null argument");
     const std::string ks(key), vs(value);
     if (ks == "precision") {
@@ -711,6 +726,8 @@ stencil_status stencil_batch_set_option(stencil_batch *batch, const char *key, c
     }
     drop_graph(batch->cache);
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_set_option");
 }
 
 // Autotuner of the batched form.  Grids are grouped into shape classes
@@ -737,7 +754,7 @@ static int size_class(const Plan &p)
 stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *ins, void *const *outs, int64_t steps,
                                       int reps, stencil_stream_t stream, stencil_batch_tune_result *results,
                                       int max_results, int *n_results)
-{
+try {
     if (n_results) *n_results = 0;
     if (steps < 1 || reps < 1) return fail(STENCIL_ERR_INVALID_ARG, "stencil_batch_autotune: steps and reps >= 1");
     Layout L0;
@@ -917,13 +934,17 @@ stencil_status stencil_batch_autotune(stencil_batch *batch, const void *const *i
     batch->ran = false;
     if (n_results) *n_results = nres;
     return s;
+} catch (...) {
+    return gbs::abi_exception("stencil_batch_autotune");
 }
 
 void stencil_batch_destroy(stencil_batch *batch)
-{
+try {
     if (!batch) return;
     drop_graph(batch->cache);
     delete batch;
+} catch (...) {
+    gbs::abi_exception("stencil_batch_destroy");
 }
 
 }  // extern "C"

@@ -160,7 +160,7 @@ const stencil_peaks &peaks() { return g_peaks; }
 using namespace gbs;
 
 extern "C" stencil_status stencil_model_predict(const stencil_model_in *in, stencil_model_out *out)
-{
+try {
     if (!in || !out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_model_predict: null pointer");
     if ((in->shape != STENCIL_BOX && in->shape != STENCIL_STAR) || in->d < 1 || in->d > 3 || in->r < 1 ||
         in->t < 1 || in->dtype_bytes < 1 || !(in->sparsity > 0 && in->sparsity <= 1) || !(in->beta >= 1) ||
@@ -186,10 +186,12 @@ extern "C" stencil_status stencil_model_predict(const stencil_model_in *in, sten
     out->gstencils_cu = m.gst_cu;
     out->gstencils_tc = m.gst_tc;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_model_predict");
 }
 
 extern "C" stencil_status stencil_set_peaks(const stencil_peaks *p)
-{
+try {
     if (!p) return fail(STENCIL_ERR_INVALID_ARG, "stencil_set_peaks: null pointer");
     const double *src = &p->hbm_bytes_per_s;
     double *dst = &g_peaks.hbm_bytes_per_s;
@@ -199,11 +201,15 @@ extern "C" stencil_status stencil_set_peaks(const stencil_peaks *p)
     for (int i = 0; i < 8; i++)
         if (src[i] > 0) dst[i] = src[i];
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_set_peaks");
 }
 
 extern "C" stencil_status stencil_get_peaks(stencil_peaks *p)
-{
+try {
     if (!p) return fail(STENCIL_ERR_INVALID_ARG, "stencil_get_peaks: null pointer");
     *p = g_peaks;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_get_peaks");
 }

@@ -14,6 +14,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
+#include <new>
+#include <stdexcept>
 #include <string>
 
 #include "internal.h"
@@ -27,6 +30,30 @@ static std::atomic<uint64_t> g_launches{0};
 stencil_status fail(stencil_status s, const std::string &msg)
 {
     g_last_error = msg;
+    return s;
+}
+
+stencil_status abi_exception(const char *entry) noexcept
+{
+    stencil_status s = STENCIL_ERR_INTERNAL;
+    const char *what = "unknown exception";
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        s = STENCIL_ERR_OOM;
+        what = "host allocation failed";
+    } catch (const std::length_error &) {
+        s = STENCIL_ERR_OOM;
+        what = "host allocation too large";
+    } catch (const std::exception &e) {
+        what = e.what();
+    } catch (...) {
+    }
+    try {
+        g_last_error = std::string(entry) + ": " + what;
+    } catch (...) {
+        g_last_error.clear();
+    }
     return s;
 }
 
@@ -377,7 +404,7 @@ extern "C" {
 
 stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int d, int r,
                                    const double *weights, stencil_dtype dtype, const int64_t *dims, int t)
-{
+try {
     if (!plan) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: plan is null");
     *plan = nullptr;
     if (!weights || !dims) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_create: weights or dims is null");
@@ -421,10 +448,12 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
     out->p = std::move(p);
     *plan = out;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_create");
 }
 
 stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, const char *value)
-{
+try {
     if (!plan || !key || !value) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_option: null argument");
     Plan trial = plan->p;
     std::string k(key), v(value);
@@ -472,6 +501,10 @@ stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, cons
     } else if (k == "debug_unmet_wait") {
         if (v != "0" && v != "1") return fail(STENCIL_ERR_INVALID_ARG, "debug_unmet_wait must be 0 or 1");
         trial.debug_unmet_wait = v == "1";
+    } else if (k == "debug_host_exception") {
+        if (v == "bad_alloc") throw std::bad_alloc();
+        if (v == "runtime") throw std::runtime_error("planted by debug_host_exception");
+        return fail(STENCIL_ERR_INVALID_ARG, "debug_host_exception must be bad_alloc or runtime");
     } else {
         return fail(STENCIL_ERR_INVALID_ARG, "unknown option key '" + k + "'");
     }
@@ -479,33 +512,42 @@ stencil_status stencil_plan_set_option(stencil_plan *plan, const char *key, cons
     if (s != STENCIL_OK) return s;
     plan->p = std::move(trial);
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_set_option");
 }
 
 stencil_status stencil_plan_info(const stencil_plan *plan, stencil_info *info)
-{
+try {
     if (!plan || !info) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_info: null argument");
     *info = plan->p.info;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_info");
 }
 
 size_t stencil_plan_workspace_bytes(const stencil_plan *plan, int for_host_io)
-{
+try {
     if (!plan) return 0;
     return plan->p.grid_bytes() * (for_host_io ? 3 : 1);
+} catch (...) {
+    gbs::abi_exception("stencil_plan_workspace_bytes");
+    return 0;
 }
 
 stencil_status stencil_plan_set_workspace(stencil_plan *plan, void *dev_ptr, size_t bytes)
-{
+try {
     if (!plan) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_workspace: plan is null");
     if (!dev_ptr && bytes > 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_set_workspace: null with bytes > 0");
     plan->p.ws = dev_ptr;
     plan->p.ws_bytes = dev_ptr ? bytes : 0;
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_set_workspace");
 }
 
 stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_tc_layout *layout, int *kb_lo,
                                       int *kb_hi, double *B)
-{
+try {
     if (!plan || !layout) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_tc_layout: null argument");
     const Plan &p = plan->p;
     if (t < 1 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_tc_layout: t must be 1..16");
@@ -538,12 +580,14 @@ stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_t
                     }
     }
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_tc_layout");
 }
 
 stencil_status stencil_plan_sptc_layout(const stencil_plan *plan, int t, stencil_sptc_layout *layout,
                                         int *chunk_first, int *chunk_second, unsigned char *line_mask,
                                         float *values, unsigned char *select)
-{
+try {
     if (!plan || !layout) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_sptc_layout: null argument");
     const Plan &p = plan->p;
     if (t < 1 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_sptc_layout: t must be 1..16");
@@ -576,6 +620,8 @@ stencil_status stencil_plan_sptc_layout(const stencil_plan *plan, int t, stencil
                     }
     }
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_plan_sptc_layout");
 }
 
 void stencil_plan_destroy(stencil_plan *plan) { delete plan; }
@@ -589,6 +635,7 @@ const char *stencil_status_string(stencil_status s)
     case STENCIL_ERR_CUDA: return "CUDA error";
     case STENCIL_ERR_OOM: return "out of memory / workspace too small";
     case STENCIL_ERR_TIMEOUT: return "device wait timed out";
+    case STENCIL_ERR_INTERNAL: return "internal error";
     }
     return "unknown status";
 }

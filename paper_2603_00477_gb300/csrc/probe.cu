@@ -54,7 +54,7 @@ stencil_status time_chains(int blocks, int iters, cudaStream_t st, double *flops
 using namespace gbs;
 
 extern "C" stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_stream_t stream)
-{
+try {
     if (!measured) return fail(STENCIL_ERR_INVALID_ARG, "stencil_probe_peaks: null pointer");
     *measured = stencil_peaks{};
     int dev = 0, sms = 0;
@@ -66,4 +66,6 @@ extern "C" stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_s
     stencil_status s = time_chains<double>(blocks, 1 << 7, st, &measured->cu_f64_flops);
     if (s != STENCIL_OK) return s;
     return time_chains<float>(blocks, 1 << 13, st, &measured->cu_f32_flops);
+} catch (...) {
+    return gbs::abi_exception("stencil_probe_peaks");
 }

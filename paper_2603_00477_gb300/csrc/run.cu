@@ -110,7 +110,7 @@ using namespace gbs;
 
 extern "C" stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_t steps,
                                       stencil_stream_t stream)
-{
+try {
     if (!plan || !in || !out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: null argument");
     if (in == out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: in and out must differ");
     if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: steps < 0");
@@ -121,11 +121,13 @@ extern "C" stencil_status stencil_run(stencil_plan *plan, const void *in, void *
         if (b < c + g && c < b + g) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run: in and out overlap");
     }
     return run_sweeps(p, in, out, p.ws, p.ws_bytes, steps, (cudaStream_t)stream);
+} catch (...) {
+    return gbs::abi_exception("stencil_run");
 }
 
 extern "C" stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out, int64_t steps,
                                            stencil_stream_t stream)
-{
+try {
     if (!plan || !host_in || !host_out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_host: null argument");
     if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_host: steps < 0");
     Plan &p = plan->p;
@@ -142,10 +144,12 @@ extern "C" stencil_status stencil_run_host(stencil_plan *plan, const void *host_
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(device -> host)");
     e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cudaStreamSynchronize");
+} catch (...) {
+    return gbs::abi_exception("stencil_run_host");
 }
 
 extern "C" stencil_status stencil_device_status(stencil_stream_t stream)
-{
+try {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_device_status: stream");
     int flag = 0;
@@ -153,6 +157,8 @@ extern "C" stencil_status stencil_device_status(stencil_stream_t stream)
     if (s != STENCIL_OK) return s;
     if (flag) return fail(STENCIL_ERR_TIMEOUT, "a tensor-core kernel's bounded wait for its MMAs ran out");
     return STENCIL_OK;
+} catch (...) {
+    return gbs::abi_exception("stencil_device_status");
 }
 
 // ---------------------------------------------------------------------------
@@ -206,7 +212,7 @@ stencil_status noalloc_scratch(void **ptr)
 
 extern "C" stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in, void *out, int64_t steps,
                                               stencil_stream_t stream)
-{
+try {
     if (!plan || !in || !out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: null argument");
     if (in == out) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: in and out must differ");
     if (steps < 0) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: steps < 0");
@@ -224,4 +230,6 @@ extern "C" stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in
     stencil_status s = noalloc_scratch(&scratch);
     if (s != STENCIL_OK) return s;
     return run_sweeps(p, in, out, scratch, kNoAllocScratchBytes, steps, (cudaStream_t)stream);
+} catch (...) {
+    return gbs::abi_exception("stencil_run_noalloc");
 }

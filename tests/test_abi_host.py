@@ -26,9 +26,32 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for s in range(6):
-        assert B.stencil_status_string(s)
+    for s in range(7):
+        assert B.stencil_status_string(s) != "unknown status"
     assert B.stencil_status_string(0) == "ok"
+    assert B.stencil_status_string(7) == "unknown status"
+
+
+@pytest.mark.parametrize("kind,status", [("bad_alloc", B.STENCIL_ERR_OOM),
+                                         ("runtime", B.STENCIL_ERR_INTERNAL)])
+def test_exception_stops_at_the_boundary(lib, kind, status):
+    """A C++ exception thrown inside the library (planted by a test hook)
+    comes back as a status and a message, the process keeps running and the
+    plan stays usable and unchanged."""
+    p = B.stencil_plan_create("box", 2, 1, _w("box", 2, 1), "f64", (64, 64), 2)
+    try:
+        before = B.stencil_plan_info(p)
+        rc = lib.stencil_plan_set_option(p, b"debug_host_exception", kind.encode())
+        assert rc == status
+        msg = B.stencil_last_error()
+        assert msg.startswith("stencil_plan_set_option: ")
+        if kind == "runtime":
+            assert "planted by debug_host_exception" in msg
+        assert B.stencil_plan_info(p) == before
+        B.stencil_plan_set_option(p, "t", 1)
+        assert B.stencil_plan_info(p)["t"] == 1
+    finally:
+        B.stencil_plan_destroy(p)
 
 
 def _w(shape, d, r):
