@@ -424,7 +424,9 @@ stencil_status stencil_model_predict(const stencil_model_in *in, stencil_model_o
 /* The roofline inputs of Sec. 3.1 (peak compute per unit and bandwidth B;
  * P_SpTC of Eq. 20).
  * Replace the process-wide peak table the dispatcher uses (zero fields
- * unchanged) / read it.  Defaults are GB300 figures. */
+ * unchanged) / read it.  Defaults are GB300 figures.  Thread safe; plans
+ * created afterwards use the new table.  INVALID_ARG (table unchanged) for
+ * a null pointer or a negative, NaN or infinite field. */
 stencil_status stencil_set_peaks(const stencil_peaks *peaks);
 stencil_status stencil_get_peaks(stencil_peaks *peaks);
 

@@ -42,7 +42,7 @@ int fused_points(int shape, int d, int r, int t);
 ModelOut model_eval(int shape, int d, int r, int t, int D, double S, double beta, double P_cu,
                     double P_tc, double B);
 
-const stencil_peaks &peaks();
+stencil_peaks peaks();  // a copy of the process-wide table (thread safe)
 
 // ---- tensor-core tile geometry (host view of what the TC kernels issue) ----
 struct TcGeometry {

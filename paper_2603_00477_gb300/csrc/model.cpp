@@ -12,6 +12,7 @@
 // multiplies the issued work like alpha/S.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -153,7 +154,22 @@ static stencil_peaks g_peaks = {
     4.5e15,                    // sptc_bf16_flops
 };
 
-const stencil_peaks &peaks() { return g_peaks; }
+// The table is process-wide and may be replaced while other threads create
+// plans: every access copies it under this lock.
+static std::mutex g_peaks_mutex;
+
+// The eight rates, in declaration order.
+static double stencil_peaks::*const kPeakFields[8] = {
+    &stencil_peaks::hbm_bytes_per_s, &stencil_peaks::cu_f64_flops,   &stencil_peaks::cu_f32_flops,
+    &stencil_peaks::tc_f64_flops,    &stencil_peaks::tc_tf32_flops,  &stencil_peaks::tc_bf16_flops,
+    &stencil_peaks::sptc_tf32_flops, &stencil_peaks::sptc_bf16_flops,
+};
+
+stencil_peaks peaks()
+{
+    std::lock_guard<std::mutex> lock(g_peaks_mutex);
+    return g_peaks;
+}
 
 }  // namespace gbs
 
@@ -193,13 +209,13 @@ try {
 extern "C" stencil_status stencil_set_peaks(const stencil_peaks *p)
 try {
     if (!p) return fail(STENCIL_ERR_INVALID_ARG, "stencil_set_peaks: null pointer");
-    const double *src = &p->hbm_bytes_per_s;
-    double *dst = &g_peaks.hbm_bytes_per_s;
-    for (int i = 0; i < 8; i++) {
-        if (src[i] < 0 || std::isnan(src[i])) return fail(STENCIL_ERR_INVALID_ARG, "stencil_set_peaks: negative");
+    for (auto f : kPeakFields) {
+        if (!(p->*f >= 0) || std::isinf(p->*f))
+            return fail(STENCIL_ERR_INVALID_ARG, "stencil_set_peaks: a rate is negative or not finite");
     }
-    for (int i = 0; i < 8; i++)
-        if (src[i] > 0) dst[i] = src[i];
+    std::lock_guard<std::mutex> lock(g_peaks_mutex);
+    for (auto f : kPeakFields)
+        if (p->*f > 0) g_peaks.*f = p->*f;
     return STENCIL_OK;
 } catch (...) {
     return gbs::abi_exception("stencil_set_peaks");
@@ -208,7 +224,7 @@ try {
 extern "C" stencil_status stencil_get_peaks(stencil_peaks *p)
 try {
     if (!p) return fail(STENCIL_ERR_INVALID_ARG, "stencil_get_peaks: null pointer");
-    *p = g_peaks;
+    *p = peaks();
     return STENCIL_OK;
 } catch (...) {
     return gbs::abi_exception("stencil_get_peaks");

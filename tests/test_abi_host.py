@@ -188,6 +188,49 @@ def test_peaks_roundtrip(lib):
         B.stencil_set_peaks(hbm_bytes_per_s=1.0e12)
         assert B.stencil_get_peaks()["hbm_bytes_per_s"] == 1.0e12
         assert B.stencil_get_peaks()["cu_f64_flops"] == old["cu_f64_flops"]  # zero fields unchanged
+        B.stencil_set_peaks(sptc_bf16_flops=7.0e15)  # the last field of the table
+        assert B.stencil_get_peaks()["sptc_bf16_flops"] == 7.0e15
+        for bad in (-1.0, float("nan"), float("inf")):
+            before = B.stencil_get_peaks()
+            with pytest.raises(B.StencilError):
+                B.stencil_set_peaks(cu_f32_flops=1e14, tc_tf32_flops=bad)
+            assert B.stencil_get_peaks() == before  # refused as a whole
+    finally:
+        B.stencil_set_peaks(**old)
+
+
+def test_peaks_table_is_thread_safe(lib):
+    """Threads replacing the table while others create plans and read it
+    never see a torn table: every read is one of the tables written."""
+    import threading
+    old = B.stencil_get_peaks()
+    tables = [dict(old, hbm_bytes_per_s=h, cu_f64_flops=h / 5) for h in (2e12, 4e12, 8e12)]
+    seen, stop = [], threading.Event()
+
+    def writer():
+        i = 0
+        while not stop.is_set():
+            B.stencil_set_peaks(**tables[i % 3])
+            i += 1
+
+    def reader():
+        for _ in range(300):
+            p = B.stencil_get_peaks()
+            seen.append(p["cu_f64_flops"] * 5 == p["hbm_bytes_per_s"])
+            h = B.stencil_plan_create("box", 2, 1, _w("box", 2, 1), "f64", (64, 64), 0)
+            B.stencil_plan_destroy(h)
+
+    try:
+        ws = [threading.Thread(target=writer) for _ in range(2)]
+        rs = [threading.Thread(target=reader) for _ in range(2)]
+        for th in ws + rs:
+            th.start()
+        for th in rs:
+            th.join()
+        stop.set()
+        for th in ws:
+            th.join()
+        assert seen and all(seen)
     finally:
         B.stencil_set_peaks(**old)
 
