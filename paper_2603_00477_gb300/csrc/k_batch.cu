@@ -379,13 +379,12 @@ stencil_status launch_batch(stencil_batch *b, const Layout &L, const void *const
         const int R = g.plan.pat.r, t = g.plan.t;
         smem = std::max(smem, batch_item_smem(g.plan.tile[1], g.plan.tile[2], t, R, es));
     }
-    static int cached64 = 0, cached32 = 0;
     const void *fn = b->dtype == STENCIL_F64 ? (const void *)bt::batch_sweeps<double> : (const void *)bt::batch_sweeps<float>;
-    stencil_status s = ensure_smem(fn, smem, b->dtype == STENCIL_F64 ? &cached64 : &cached32);
+    stencil_status s = ensure_smem(fn, smem);
     if (s != STENCIL_OK) return s;
     int occ = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, bt::kThreads, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "batch: occupancy");
+    s = occupancy(fn, bt::kThreads, smem, &occ);
+    if (s != STENCIL_OK) return s;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)std::min<int64_t>(L.nitems, (int64_t)std::max(1, occ) * sms);

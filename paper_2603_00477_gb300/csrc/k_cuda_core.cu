@@ -5,7 +5,11 @@
 // FP32.
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
+#include <utility>
 
 #include "k_cuda_core_impl.cuh"
 
@@ -16,12 +20,46 @@ stencil_status cuda_fail(cudaError_t e, const char *what)
     return fail(STENCIL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-stencil_status ensure_smem(const void *func, size_t bytes, int *cached)
+namespace {
+// Launch facts shared by every thread of the process: the dynamic
+// shared-memory limit already set per (kernel, device), and resident blocks
+// per SM per (kernel, device, threads, smem).  The limit only grows, and
+// only under the lock, so it is never below what a launch was promised.
+std::mutex g_launch_mu;
+std::map<std::pair<const void *, int>, int> g_smem_limit;
+std::map<std::tuple<const void *, int, int, size_t>, int> g_occupancy;
+}  // namespace
+
+stencil_status ensure_smem(const void *func, size_t bytes)
 {
-    if (bytes <= 48 * 1024 || (int)bytes <= *cached) return STENCIL_OK;
-    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (bytes <= 48 * 1024) return STENCIL_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_launch_mu);
+    int &limit = g_smem_limit[std::make_pair(func, dev)];
+    if ((int)bytes <= limit) return STENCIL_OK;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(max dynamic smem)");
-    *cached = (int)bytes;
+    limit = (int)bytes;
+    return STENCIL_OK;
+}
+
+stencil_status occupancy(const void *func, int threads, size_t smem, int *blocks)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lock(g_launch_mu);
+    const auto key = std::make_tuple(func, dev, threads, smem);
+    auto it = g_occupancy.find(key);
+    if (it == g_occupancy.end()) {
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, threads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        it = g_occupancy.emplace(key, b).first;
+    }
+    *blocks = it->second;
     return STENCIL_OK;
 }
 

@@ -48,8 +48,6 @@ template <typename T, int SHAPE, int R>
 stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int band, cudaStream_t st)
 {
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 2, R>::K>;
-    static int cached = 0;
-    static int occ_smem = -1, occ_blocks = 0;
     Wt wt;
     for (int k = 0; k < cu::Taps<SHAPE, 2, R>::K; k++) wt.w[k] = (T)p.w[k];
     int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
@@ -61,13 +59,11 @@ stencil_status launch2d(const Plan &p, const void *in, void *out, int t, int ban
     const size_t smem = cu::weight_smem_bytes<T, cu::Taps<SHAPE, 2, R>::K>() + bufb * (t > 1 ? 3 : 2);
     if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
     auto kern = cu::cu2d_sweep<T, SHAPE, R, kV<T>>;
-    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    stencil_status s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
-    if (occ_smem != (int)smem) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        occ_smem = (int)smem;
-    }
+    int occ_blocks = 0;
+    s = occupancy((const void *)kern, cu::kThreads, smem, &occ_blocks);
+    if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -97,19 +93,16 @@ template <typename T, int SHAPE, int R>
 stencil_status launch3d_stream(const Plan &p, const void *in, void *out, cudaStream_t st)
 {
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
-    static int cached = 0;
-    static int occ = -1;
     Wt wt;
     for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];
     const size_t smem = cu::stream_smem_bytes<T, R>(cu::Taps<SHAPE, 3, R>::K);
     if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "3-D streaming tile does not fit in shared memory");
     auto kern = cu::cu3d_stream<T, SHAPE, R>;
-    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    stencil_status s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
-    if (occ < 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, cu::kThreads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    }
+    int occ = 0;
+    s = occupancy((const void *)kern, cu::kThreads, smem, &occ);
+    if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -131,8 +124,6 @@ stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStr
 {
     if (t == 1) return launch3d_stream<T, SHAPE, R>(p, in, out, st);
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
-    static int cached = 0;
-    static int occ_smem = -1, occ_blocks = 0;
     Wt wt;
     for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];
     int tile[3] = {p.tile[0], p.tile[1], p.tile[2]};
@@ -143,13 +134,11 @@ stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStr
         cu::weight_smem_bytes<T, cu::Taps<SHAPE, 3, R>::K>() + Z * H * W * sizeof(T) * (t > 1 ? 3 : 2);
     if (smem > kMaxSmem) return fail(STENCIL_ERR_UNSUPPORTED, "CUDA-core tile does not fit in shared memory");
     auto kern = cu::cu3d_sweep<T, SHAPE, R, kV<T>>;
-    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    stencil_status s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
-    if (occ_smem != (int)smem) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_blocks, kern, cu::kThreads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        occ_smem = (int)smem;
-    }
+    int occ_blocks = 0;
+    s = occupancy((const void *)kern, cu::kThreads, smem, &occ_blocks);
+    if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -310,7 +310,6 @@ __global__ void __launch_bounds__(256, 2) sptc2d_sweep(const float *__restrict__
 template <int NS, int LC, bool FULL>
 stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t ny, int64_t nx, cudaStream_t st)
 {
-    static int cached = 0;
     const size_t table = (size_t)sp.lines * NS * 32 * 20;
     const size_t tile = (size_t)(kSpTY + 2 * sp.R) * sp.pitch_q * 16;
     // double-buffered input tiles when two CTAs still fit on an SM, else one
@@ -320,20 +319,20 @@ stencil_status launch_ns(const SpParams &sp, const void *in, void *out, int64_t 
     const size_t smem = table + sp2.nbuf * tile;
     if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core tile does not fit in shared memory");
     auto kern = sptc2d_sweep<NS, LC, FULL>;
-    stencil_status s = ensure_smem((const void *)kern, smem, &cached);
+    stencil_status s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "sptc2d_sweep occupancy");
+    s = occupancy((const void *)kern, 256, smem, &per_sm);
+    if (s != STENCIL_OK) return s;
     if (per_sm < 1) return fail(STENCIL_ERR_UNSUPPORTED, "sparse tensor-core kernel cannot be resident");
     const int64_t nty = (ny + kSpTY - 1) / kSpTY, ntx = (nx + sp.xshift + kSpTX - 1) / kSpTX, ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per_sm);
     kern<<<grid, 256, smem, st>>>((const float *)in, (float *)out, sp2, (int)ntiles, (int)ntx);
     note_launch();
-    e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "sptc2d_sweep launch");
 }
 

@@ -676,7 +676,6 @@ stencil_status launch_tc2d(const Plan &p, const void *in, void *out, int t, cuda
 {
     using namespace tcs;
     constexpr int ES = Elem<PREC>::bytes, E = 16 / ES, KI = 2 * E, TX = NACC * TN;
-    static int cached = 0;
     TcParams tp;
     TcLines L;
     stencil_status s = fill_params(p, t, TN, KI, &tp, &L);
@@ -694,7 +693,7 @@ stencil_status launch_tc2d(const Plan &p, const void *in, void *out, int t, cuda
     smem += 128;  // TMEM address and mbarrier in front of the operands
     if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core tile does not fit in shared memory");
     auto kern = tc2d_sweep<PREC, NACC>;
-    s = ensure_smem((const void *)kern, smem, &cached);
+    s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
     const int64_t ny = p.dims[1], nx = p.dims[2];
     dim3 grid((unsigned)((nx + TX - 1) / TX), (unsigned)((ny + TM - 1) / TM));
@@ -709,7 +708,6 @@ stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t,
 {
     using namespace tcs;
     constexpr int TX = NACC * TN_;
-    static int cached = 0;
     TcParams tp;
     TcLines L;
     stencil_status s = fill_params(p, t, TN_, 8, &tp, &L);
@@ -725,7 +723,7 @@ stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t,
     *fits = smem <= 227 * 1024;
     if (!*fits) return STENCIL_OK;
     auto kern = tc2d_ws<PREC, TN_, NACC>;
-    s = ensure_smem((const void *)kern, smem, &cached);
+    s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -763,7 +761,6 @@ stencil_status launch_tc2d_ws(const Plan &p, const void *in, void *out, int t, c
 stencil_status launch_dmma2d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
     using namespace tcs;
-    static int cached = 0;
     TcParams tp;
     TcLines L;
     stencil_status s = fill_params(p, t, 8, 4, &tp, &L);
@@ -775,7 +772,7 @@ stencil_status launch_dmma2d(const Plan &p, const void *in, void *out, int t, cu
     const int W = DM_T + tp.nch, H = DM_T + 2 * R;
     const size_t smem = ((size_t)H * W + (size_t)(2 * R + 1) * L.nkb * 32) * 8;
     if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "FP64 MMA tile does not fit in shared memory");
-    s = ensure_smem((const void *)dmma2d_sweep, smem, &cached);
+    s = ensure_smem((const void *)dmma2d_sweep, smem);
     if (s != STENCIL_OK) return s;
     const int64_t ny = p.dims[1], nx = p.dims[2];
     dim3 grid((unsigned)((nx + DM_T - 1) / DM_T), (unsigned)((ny + DM_T - 1) / DM_T));

@@ -36,8 +36,15 @@ stencil_status launch_halo_copy(const Plan &p, const void *in, void *out, void *
 stencil_status run_sweeps(Plan &p, const void *in, void *out, void *ws, size_t ws_bytes, int64_t steps,
                           cudaStream_t st);
 
-// Raise the dynamic shared-memory limit of `func` to `bytes` once.
-stencil_status ensure_smem(const void *func, size_t bytes, int *cached);
+// Raise the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes` (once per kernel and device; thread safe).
+stencil_status ensure_smem(const void *func, size_t bytes);
+
+// Blocks of kernel `func` resident per SM of the current device with
+// `threads` threads and `smem` bytes of dynamic shared memory (after
+// ensure_smem); computed once per (kernel, device, threads, smem) and
+// cached for the process (thread safe).
+stencil_status occupancy(const void *func, int threads, size_t smem, int *blocks);
 
 stencil_status cuda_fail(cudaError_t e, const char *what);
 
