@@ -34,7 +34,9 @@
  *     launched on it and the call returns without synchronising; a CUDA
  *     error reported at launch gives STENCIL_ERR_CUDA, and an asynchronous
  *     fault surfaces as STENCIL_ERR_CUDA on a later call.
- *   - A plan is not thread safe: use one plan per stream.
+ *   - A plan or batch is not thread safe: use one per stream (and thread).
+ *     Library-wide state (the peak table, per-kernel launch settings, the
+ *     launch counter, the last-error message per thread) is.
  *   - stencil_last_error() returns a human-readable message for the last
  *     failed call of the calling thread.
  */
