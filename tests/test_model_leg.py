@@ -122,3 +122,29 @@ def test_paper_cases(leg):
         P_tc = leg["peaks"]["tc_f64_flops" if D == 8 else "sptc_tf32_flops"]
         assert case["scenario"] == model.scenario(shape, d, r, p["t"], D, S, P_cu, P_tc, HBM)
         assert tc["intensity"] == pytest.approx(model.I_tc(shape, d, r, p["t"], D, S), rel=1e-12)
+
+
+def test_cli_prints_one_json_line():
+    """`bench.py --leg model` needs no GPU and prints one JSON line."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--leg", "model"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert res.returncode == 0, res.stderr
+    lines = [l for l in res.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    assert out["leg"] == "model" and len(out["cases"]) == 6
+    assert set(out["classification"]) == {"f32", "f64"}
+
+
+def test_kernel_names():
+    bench = importlib.import_module("bench")
+    assert bench.kernel_name({"path": 1, "t": 1, "precision_name": "native"}, 2, "f64") == "cu2d_sweep"
+    assert bench.kernel_name({"path": 1, "t": 1, "precision_name": "native"}, 3, "f32") == "cu3d_stream"
+    assert bench.kernel_name({"path": 1, "t": 2, "precision_name": "native"}, 3, "f64") == "cu3d_sweep"
+    assert bench.kernel_name({"path": 2, "t": 2, "precision_name": "native"}, 2, "f64") == "dmma2d_sweep"
+    assert bench.kernel_name({"path": 2, "t": 4, "precision_name": "tf32"}, 2, "f32") == "tc2d_ws"
+    assert bench.kernel_name({"path": 2, "t": 2, "precision_name": "bf16x3"}, 2, "f32") == "tc2d_sweep"
+    assert bench.kernel_name({"path": 3, "t": 3, "precision_name": "tf32"}, 2, "f32") == "sptc2d_sweep"
