@@ -682,16 +682,30 @@ def main():
         plan.run_host(h_in, h_out, steps)  # warm (workspace of three grids)
         torch.cuda.synchronize()
         barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            plan.run_host(h_in, h_out, steps)
-        el = time.perf_counter() - t0
+        e2e_clocks = ClockSampler(local_rank)
+        with e2e_clocks:
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                plan.run_host(h_in, h_out, steps)
+            el = time.perf_counter() - t0
         el = max_over_ranks(el, world)
         nbytes = h_in.numel() * h_in.element_size()
         e2e = {"value": whole_job_rate(world, pts, steps, args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "api": "stencil_run_host (pinned host buffers)"}
-        del h_in, h_out
+               "api": "stencil_run_host (pinned host buffers)", "clocks": e2e_clocks.summary()}
+        # the copy rates of the same pinned buffers alone (CUDA events), which
+        # split the end-to-end time into copies and compute
+        d_buf = torch.empty(tuple(h_in.shape), dtype=h_in.dtype, device=x.device)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        d_buf.copy_(h_in, non_blocking=True)
+        ev[1].record(stream)
+        h_out.copy_(d_buf, non_blocking=True)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        e2e["h2d_gbs"] = nbytes / (max(ev[0].elapsed_time(ev[1]), 1e-6) / 1e3) / 1e9
+        e2e["d2h_gbs"] = nbytes / (max(ev[1].elapsed_time(ev[2]), 1e-6) / 1e3) / 1e9
+        del h_in, h_out, d_buf
         plan._ws = None
         torch.cuda.empty_cache()
         plan.ensure_workspace(x.device)
