@@ -355,6 +355,16 @@ def declared_symbols(header: str | None = None) -> list[str]:
 
 # ---- convenience wrapper over torch tensors ----------------------------------------
 
+def _resolve_device(device):
+    """torch.device with the index filled in ("cuda" -> the current CUDA
+    device), so that it compares equal to the device of a tensor on it."""
+    import torch
+    dev = torch.device(device)
+    if dev.type == "cuda" and dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    return dev
+
+
 class Plan:
     """A plan plus PyTorch-allocated workspace.  run() takes CUDA tensors of
     the stored shape (interior + 2r per axis) and the plan's dtype."""
@@ -384,8 +394,9 @@ class Plan:
 
     def ensure_workspace(self, device, host_io: bool = False):
         import torch
+        device = _resolve_device(device)
         need = stencil_plan_workspace_bytes(self.handle, host_io)
-        if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device(device):
+        if self._ws is None or self._ws.numel() < need or self._ws.device != device:
             self._ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
             stencil_plan_set_workspace(self.handle, self._ws.data_ptr(), self._ws.numel())
         return self._ws
