@@ -113,6 +113,11 @@ def test_run_argument_checks_launch_nothing(lib):
         with pytest.raises(B.StencilError) as e:
             B.stencil_run_host(p, 4096, 1 << 20, 1, 0)
         assert e.value.status == B.STENCIL_ERR_OOM
+        for steps, reps in ((0, 1), (3, 0)):  # the autotuner checks before any CUDA call
+            with pytest.raises(B.StencilError) as e:
+                B.stencil_plan_autotune(p, 4096, 1 << 20, steps, reps, 0)
+            assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        assert lib.stencil_plan_autotune(None, None, None, 1, 1, None, None, 0, None) == B.STENCIL_ERR_INVALID_ARG
         assert B.stencil_launch_count() == n0
     finally:
         B.stencil_plan_destroy(p)
@@ -288,6 +293,17 @@ def test_batch_workspace_and_no_launch_without_it(lib):
         with pytest.raises(B.StencilError) as e:
             B.stencil_batch_run(h, [4096, 8192], [1 << 20, 1 << 21], 9, 0)
         assert e.value.status == B.STENCIL_ERR_OOM
+        # the autotuner refuses the same way, and bad counts, before any CUDA call
+        with pytest.raises(B.StencilError) as e:
+            B.stencil_batch_autotune(h, [4096, 8192], [1 << 20, 1 << 21], 9, 1, 0)
+        assert e.value.status == B.STENCIL_ERR_OOM
+        for steps, reps in ((0, 1), (9, 0)):
+            with pytest.raises(B.StencilError) as e:
+                B.stencil_batch_autotune(h, [4096, 8192], [1 << 20, 1 << 21], steps, reps, 0)
+            assert e.value.status == B.STENCIL_ERR_INVALID_ARG
+        with pytest.raises(B.StencilError) as e:  # a grid's in and out are the same buffer
+            B.stencil_batch_run(h, [4096, 8192], [4096, 1 << 21], 9, 0)
+        assert e.value.status == B.STENCIL_ERR_INVALID_ARG
         assert B.stencil_launch_count() == n0
     finally:
         B.stencil_batch_destroy(h)
