@@ -171,3 +171,97 @@ def test_K_fused_star_closed_form_small_cases():
     # star 3D r=1: octahedron sizes 7, 25, 63
     assert [model.K_fused("star", 3, 1, t) for t in (1, 2, 3)] == [7, 25, 63]
     assert model.K_fused("star", 3, 2, 2) == 73
+
+
+# ---------------------------------------------------------------------------
+# Roof functions and the beta (split-product) terms, against values worked out
+# by hand from the closed form of the roofline in point updates per second
+# (Sec. 3.1, Eq. 5; Eq. 8 for CUDA cores; Eq. 11-12 for tensor cores):
+#     CU:  min(P_CU / (2K),                t B / (2D))
+#     TC:  min(S P_TC / (2K alpha beta),   t B / (2D))
+# at the A100 peaks of tests/golden/paper_table3.json (B = 1.935e12 B/s,
+# FP64 P_CU = 9.7e12, P_TC = 19.5e12, sparse TF32 312e12 FLOP/s).
+# ---------------------------------------------------------------------------
+A100_B = 1.935e12
+
+
+def test_gstencils_roof_cu_memory_term_binds_case1():
+    """Table 3 case 1, Box-2D1R t=3 FP64: K = 9, 2K = 18 FLOP per point-step.
+    Compute term 9.7e12 / 18 = 5.3889e11; memory term 3 * 1.935e12 / 16 =
+    3.628125e11 points/s, the smaller one.  Dividing by C^(t) = 3 * 18 instead
+    of C = 18 would give 1.796e11; dropping t from the memory term 1.209e11."""
+    got = model.gstencils_roof_cu("box", 2, 1, 3, 8, 9.7e12, A100_B)
+    assert got == pytest.approx(3.628125e11, rel=1e-12)
+
+
+def test_gstencils_roof_cu_compute_term_binds_case2():
+    """Table 3 case 2, Box-2D3R t=1 FP64: K = 49; I = 49/8 = 6.125 is above
+    the ridge 9.7/1.935 = 5.013, so the roof is 9.7e12 / 98 = 9.897959e10."""
+    got = model.gstencils_roof_cu("box", 2, 3, 1, 8, 9.7e12, A100_B)
+    assert got == pytest.approx(9.7e12 / 98, rel=1e-12)
+    assert got == pytest.approx(9.8979591836734694e10, rel=1e-12)
+    # t = 2: compute term unchanged (9.898e10) and the memory term doubles
+    # (2.419e11), so the roof stays the compute term
+    assert model.gstencils_roof_cu("box", 2, 3, 2, 8, 9.7e12, A100_B) == pytest.approx(9.8979591836734694e10)
+
+
+def test_gstencils_roof_tc_compute_term_binds_case1():
+    """Case 1 on the FP64 MMA: S = 1/2, alpha = 49/27, beta = 1.
+    I_TC = 3 (49/27)/(1/2) * 9/8 = 12.25 > ridge 10.08, so the roof is
+    S P_TC / (2K alpha) = 0.5 * 19.5e12 / (18 * 49/27) = 2.984694e11."""
+    got = model.gstencils_roof_tc("box", 2, 1, 3, 8, 0.5, 19.5e12, A100_B)
+    assert got == pytest.approx(0.5 * 19.5e12 * 27 / (18 * 49), rel=1e-12)
+    assert got == pytest.approx(2.9846938775510204e11, rel=1e-12)
+
+
+def test_gstencils_roof_tc_memory_term_binds_case3():
+    """Case 3, Box-2D1R t=7 FP32 on sparse TF32: S = 15/32, alpha = 225/63,
+    I_TC = 120 < ridge 161.2, so the memory term binds: 7 * 1.935e12 / 8 =
+    1.693125e12 points/s, independent of S and alpha (they cancel between
+    I_TC and S/alpha)."""
+    got = model.gstencils_roof_tc("box", 2, 1, 7, 4, 15 / 32, 312e12, A100_B)
+    assert got == pytest.approx(1.693125e12, rel=1e-12)
+    # the same configuration with the compute term binding: half the dense
+    # TF32 peak 78e12 puts the ridge at 40.3 < 120, roof
+    # (15/32) 78e12 / (18 * 225/63) = 5.6875e11
+    got_cb = model.gstencils_roof_tc("box", 2, 1, 7, 4, 15 / 32, 78e12, A100_B)
+    assert got_cb == pytest.approx((15 / 32) * 78e12 * 63 / (18 * 225), rel=1e-12)
+    assert got_cb == pytest.approx(5.6875e11, rel=1e-12)
+
+
+def test_beta_terms_hand_values():
+    """beta = 3 (hi/lo split, three products per useful product), case 1 on the
+    FP64 MMA: C_TC = beta alpha/S t 2K = 3 * (49/27) / 0.5 * 54 = 588 FLOP and
+    I_TC = 588 / 16 = 36.75 FLOP/B; the roof is the compute term divided by
+    beta: 2.984694e11 / 3 = 9.948980e10 points/s."""
+    assert model.C_tc("box", 2, 1, 3, 0.5, beta=3.0) == pytest.approx(588.0, rel=1e-12)
+    assert model.C_tc("box", 2, 1, 3, 0.5) == pytest.approx(196.0, rel=1e-12)
+    assert model.I_tc("box", 2, 1, 3, 8, 0.5, beta=3.0) == pytest.approx(36.75, rel=1e-12)
+    assert model.P_tc_actual("box", 2, 1, 3, 8, 0.5, 19.5e12, A100_B, beta=3.0) == pytest.approx(
+        0.5 * 19.5e12 * 27 / (49 * 3), rel=1e-12)
+    assert model.gstencils_roof_tc("box", 2, 1, 3, 8, 0.5, 19.5e12, A100_B, beta=3.0) == pytest.approx(
+        9.9489795918367347e10, rel=1e-12)
+
+
+def test_beta_cancels_when_memory_bound_and_moves_the_scenario():
+    """Case 3 with beta = 3 and the sparse TF32 peak: I_TC = 3 * 120 = 360 is
+    now above the ridge 161.2, so the compute term binds:
+    (15/32) 312e12 / (18 * (225/63) * 3) = 7.583333e11 points/s (beta applied
+    in the roof AND in I_TC; applying it only in I_TC gives 2.275e12, only in
+    the S/(alpha beta) factor 5.644e11).  With beta = 3 but the peak raised 10x (ridge 1612 > 360) the
+    roof is the memory term again and beta drops out: 1.693125e12."""
+    got = model.gstencils_roof_tc("box", 2, 1, 7, 4, 15 / 32, 312e12, A100_B, beta=3.0)
+    assert got == pytest.approx((15 / 32) * 312e12 * 63 / (18 * 225 * 3), rel=1e-12)
+    assert got == pytest.approx(7.5833333333333333e11, rel=1e-12)
+    assert model.scenario("box", 2, 1, 7, 4, 15 / 32, 19.5e12, 312e12, A100_B) == 3
+    assert model.scenario("box", 2, 1, 7, 4, 15 / 32, 19.5e12, 312e12, A100_B, beta=3.0) == 4
+    assert model.gstencils_roof_tc("box", 2, 1, 7, 4, 15 / 32, 3120e12, A100_B, beta=3.0) == pytest.approx(
+        1.693125e12, rel=1e-12)
+
+
+def test_beta_in_sweet_spot_condition():
+    """Eq. 19 with beta folded into alpha: Box-2D3R t=1 (alpha = 1), S = 1/2,
+    P_TC/P_CU = 19.5/9.7: alpha beta < S P_TC/P_CU holds for beta = 1
+    (1 < 1.00515) and fails for beta = 3 (3 > 1.00515)."""
+    assert model.alpha_condition("box", 2, 3, 1, 0.5, 9.7e12, 19.5e12)
+    assert not model.alpha_condition("box", 2, 3, 1, 0.5, 9.7e12, 19.5e12, beta=3.0)
