@@ -542,8 +542,9 @@ class Batch:
 
     def ensure_workspace(self, steps, device="cuda"):
         import torch
+        device = _resolve_device(device)
         need = stencil_batch_workspace_bytes(self.handle, steps)
-        if self._ws is None or self._ws.numel() < need:
+        if self._ws is None or self._ws.numel() < need or self._ws.device != device:
             self._ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
             stencil_batch_set_workspace(self.handle, self._ws.data_ptr(), self._ws.numel())
         return self._ws

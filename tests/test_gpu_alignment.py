@@ -12,7 +12,7 @@ import oracle
 from paper_2603_00477_gb300 import binding as B
 from paper_2603_00477_gb300 import inputs
 
-from tc_bounds import tc_bound
+from tc_bounds import sp_bound, tc_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -26,15 +26,12 @@ def torch():
     return _t
 
 
-def _bound(path, prec, plan, steps, t):
+def _bound(path, prec, plan, shape, r, steps, t):
     if path == "cuda_core":
         return 1e-5
     if path == "sparse_tensor_core":
-        mask = B.stencil_plan_sptc_layout(plan.handle, t)[3]
-        n_mma = int(sum(bin(int(m)).count("1") for m in mask))
-        sweeps = steps // t + (1 if steps % t else 0)
-        return sweeps * (2.0 * 2 ** -11 + n_mma * 2.0 ** -23)
-    return tc_bound(prec, steps, t, plan.handle)
+        return sp_bound(plan.handle, shape, r, steps, t)
+    return tc_bound(prec, steps, t, plan.handle, shape, r)
 
 
 def _run(torch, plan, u, steps, offset):
@@ -74,7 +71,7 @@ def test_aligned_and_unaligned_staging_agree(torch, path, prec, shape, r, dims, 
     if prec != "native":
         plan.set_option("precision", prec)
     plan.set_option("path", path)
-    bound = _bound(path, prec, plan, steps, t)
+    bound = _bound(path, prec, plan, shape, r, steps, t)
     ref = oracle.run(shape, 2, r, w, dims, u.astype(np.float64), steps)
     inner = tuple(slice(r, r + n) for n in dims)
     outs = []

@@ -129,19 +129,16 @@ def _size_class(ny, nx):
 def _bound(info, shape, r, w, ny, nx, steps):
     """Tolerance of a grid's result: FP32 CUDA cores 1e-5; a tensor-core form
     its derived bound."""
-    from tc_bounds import tc_bound
+    from tc_bounds import sp_bound, tc_bound
     if info["path"] == B.PATH_CUDA_CORE:
         return 1e-5
     plan = B.Plan(shape, 2, r, w, "f32", (ny, nx), info["t"])
     form = B.PREC_NAMES[info["precision"]]
     if info["path"] == B.PATH_SPARSE_TENSOR_CORE:
-        mask = B.stencil_plan_sptc_layout(plan.handle, info["t"])[3]
-        n_mma = int(sum(bin(int(m)).count("1") for m in mask))
-        sweeps = steps // info["t"] + (1 if steps % info["t"] else 0)
-        b = sweeps * (2.0 * 2 ** -11 + n_mma * 2.0 ** -23)
+        b = sp_bound(plan.handle, shape, r, steps, info["t"])
     else:
         plan.set_option("precision", form)
-        b = tc_bound(form, steps, info["t"], plan.handle)
+        b = tc_bound(form, steps, info["t"], plan.handle, shape, r)
     plan.close()
     return b
 

@@ -60,6 +60,6 @@ def test_error_growth(problem, path, prec, t):
             assert e <= 1e-5, (k, e)
         else:
             # runs of 100 steps restart the fused schedule: 100 = q*t + rem
-            per_run = tc_bound(prec, 100, t, plan.handle)
+            per_run = tc_bound(prec, 100, t, plan.handle, "box", 2)
             assert e <= per_run * k / 100, (k, e, per_run)
     plan.close()

@@ -4,7 +4,8 @@ paper Sec. 4.3) against the FP64 oracle, through the C ABI.
 Tolerance (normwise relative L-infinity over the interior), derived like the
 dense TF32 form's: per fused sweep the operands are rounded to TF32
 (P = 2 * 2^-11) and every sparse MMA adds into an FP32 accumulator
-(n_mma * 2^-23, n_mma = issued sparse instructions per output); with positive
+(n_mma * 2^-23, n_mma = an upper bound of the sparse instructions per output
+counted from the band geometry, tests/tc_bounds.py); with positive
 weights summing to 1 the errors add over sweeps.  Dyadic weights on small
 integers are exact and must match bit for bit.
 """
@@ -14,6 +15,8 @@ import pytest
 import oracle
 from paper_2603_00477_gb300 import binding as B
 from paper_2603_00477_gb300 import inputs
+
+from tc_bounds import sp_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -27,20 +30,13 @@ def torch():
     return _t
 
 
-def sp_bound(plan_handle, steps, t):
-    sweeps = steps // t + (1 if steps % t else 0)
-    mask = B.stencil_plan_sptc_layout(plan_handle, t)[3]
-    n_mma = int(sum(bin(int(m)).count("1") for m in mask))
-    return sweeps * (2.0 * 2 ** -11 + n_mma * 2.0 ** -23)
-
-
 def sp_run(torch, shape, r, w, dims, u, steps, t):
     plan = B.Plan(shape, 2, r, w, "f32", dims, t)
     plan.set_option("precision", "tf32")
     plan.set_option("path", "sparse_tensor_core")
     info = plan.info()
     assert info["path"] == B.PATH_SPARSE_TENSOR_CORE and info["t"] == t
-    bound = sp_bound(plan.handle, steps, t)
+    bound = sp_bound(plan.handle, shape, r, steps, t)
     x = torch.from_numpy(np.ascontiguousarray(u)).cuda()
     y = torch.full_like(x, float("nan"))
     n0 = B.stencil_launch_count()
@@ -113,7 +109,7 @@ def test_config_box2d2r_16384_sparse_sampled(torch, t):
     plan = B.Plan("box", 2, 2, w, "f32", dims, t)
     plan.set_option("precision", "tf32")
     plan.set_option("path", "sparse_tensor_core")
-    bound = sp_bound(plan.handle, 40, t)
+    bound = sp_bound(plan.handle, "box", 2, 40, t)
     x = torch.from_numpy(u).cuda()
     y = torch.empty_like(x)
     plan.run(x, y, 40)

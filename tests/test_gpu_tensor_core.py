@@ -145,7 +145,7 @@ def test_config_box2d2r_16384_f32_sampled(torch, prec, t):
     plan = B.Plan("box", 2, 2, w, "f32", dims, t)
     plan.set_option("precision", prec)
     plan.set_option("path", "tensor_core")
-    bound = tc_bound(prec, 40, t, plan.handle)
+    bound = tc_bound(prec, 40, t, plan.handle, "box", 2)
     plan.close()
     y = _run_big(torch, "box", 2, w, dims, u, 40, "f32", prec, t)
     u64 = u.astype(np.float64)

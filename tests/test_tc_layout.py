@@ -108,3 +108,45 @@ def test_layout_rejects_unsupported():
         B.stencil_plan_tc_layout(p.handle, 5)  # R = 15 > 12
     assert e.value.status == B.STENCIL_ERR_UNSUPPORTED
     p.close()
+
+
+@pytest.mark.parametrize("shape,r,t,dtype,prec", CASES + [("star", 2, 4, "f32", "tf32"), ("box", 3, 4, "f32", "tf32"),
+                                                          ("star", 6, 2, "f32", "tf32x3")])
+def test_tolerance_mma_count_is_the_band_count(shape, r, t, dtype, prec):
+    """The MMA count the tensor-core tolerances use (tests/tc_bounds.py) comes
+    from the band geometry alone, and the library's layout issues exactly it:
+    a kernel issuing extra MMAs cannot loosen its own tolerance.  Pinned
+    against S: Box-2D2R TF32 with N = 32, K = 8 issues 5 blocks of 8 per
+    line at t = 1 (S = 5/40) and 6 at t = 4 (S = 17/48)."""
+    from tc_bounds import dense_mma_per_output, line_half
+    p, _ = _plan(shape, r, dtype, prec)
+    lay, lo, hi, _ = B.stencil_plan_tc_layout(p.handle, t, with_B=False)
+    n = dense_mma_per_output(shape, r, t, lay["n_tile"], lay["k_inst"])
+    assert sum(max(0, h - l + 1) for l, h in zip(lo, hi)) == n
+    useful = sum(2 * line_half(shape, r, t, a) + 1 for a in range(-t * r, t * r + 1) if line_half(shape, r, t, a) >= 0)
+    assert lay["sparsity"] == pytest.approx(useful / (n * lay["k_inst"]))
+    p.close()
+    assert dense_mma_per_output("box", 2, 1, 32, 8) == 5 * 5
+    assert dense_mma_per_output("box", 2, 4, 32, 8) == 17 * 6
+
+
+@pytest.mark.parametrize("shape,r,t", [("box", 2, 1), ("box", 2, 2), ("box", 2, 3), ("box", 2, 4), ("star", 2, 3),
+                                       ("star", 6, 2), ("box", 3, 4), ("box", 7, 1), ("box", 1, 3)])
+def test_sparse_tolerance_count_bounds_the_layout(shape, r, t):
+    """The sparse tolerance's instruction count (ceil(nc/2) per non-empty line,
+    nc = ceil((16 + 2R)/4) chunks: every chunk paired with a dummy at worst)
+    is an upper bound of what the layout issues.  For Box-2D2R the layout
+    issues what the pinned S gives: t = 1..3 two instructions per line
+    (25/160, 81/288, 169/416), t = 4 three (289/816)."""
+    from tc_bounds import sparse_mma_bound
+    w = inputs.weights(shape, 2, r, seed=31)
+    p = B.Plan(shape, 2, r, w, "f32", (40, 50), t)
+    mask = B.stencil_plan_sptc_layout(p.handle, t)[3]
+    p.close()
+    issued = int(sum(bin(int(m)).count("1") for m in mask))
+    assert issued <= sparse_mma_bound(shape, r, t)
+    assert [sparse_mma_bound("box", 2, tt) for tt in (1, 2, 3, 4)] == [5 * 3, 9 * 3, 13 * 4, 17 * 4]
+    if (shape, r) == ("box", 2):
+        useful = {1: 25, 2: 81, 3: 169, 4: 289}[t]
+        S = {1: 25 / 160, 2: 81 / 288, 3: 169 / 416, 4: 289 / 816}[t]
+        assert issued == round(useful / S / 16)
