@@ -248,13 +248,21 @@ stencil_status stencil_plan_tc_layout(const stencil_plan *plan, int t, stencil_t
  * but the ping-pong buffer between fused sweeps is a 64 MiB static device
  * array of this library instead of the plan's workspace (each GPU that loads
  * the library holds it until the process exits).  Grids whose stored size
- * (halo included) exceeds 64 MiB are rejected with STENCIL_ERR_UNSUPPORTED.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and it keeps the previous call's
- * contents (nothing in it needs to start at zero: every cell a sweep reads is
- * written earlier in the same call); calls that overlap on the GPU, from any
- * stream or thread, race on it. */
+ * (halo included) exceeds 64 MiB are rejected with STENCIL_ERR_UNSUPPORTED
+ * when the run takes more than one fused sweep (a run of at most one sweep,
+ * steps <= t, uses no scratch and takes any size).  in and out must be device
+ * (or managed) memory of the current device: the array used is the current
+ * device's; other buffers are rejected with STENCIL_ERR_INVALID_ARG.  Outside
+ * a stream capture every call looks up the array's device address on the
+ * current device (so a device reset cannot leave a stale one); during a
+ * capture the address of an earlier call on that device is used, so make the
+ * first call on each device before any stream capture.  All calls share the
+ * one array; after a call returns its contents are unspecified (nothing in
+ * it needs to start at zero: every cell a sweep reads is written earlier in
+ * the same call).  Calls that overlap on the GPU, from any stream or thread,
+ * race on it; the library adds no ordering between streams, so a caller
+ * using several streams orders the calls itself (an event or a
+ * synchronisation between them). */
 stencil_status stencil_run_noalloc(stencil_plan *plan, const void *in, void *out, int64_t steps,
                                    stencil_stream_t stream);
 

@@ -62,10 +62,13 @@ try {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_probe_peaks: device query");
     cudaStream_t st = (cudaStream_t)stream;
-    const int blocks = sms * 8;  // 64 warps per SM, 16 independent chains each
-    stencil_status s = time_chains<double>(blocks, 1 << 7, st, &measured->cu_f64_flops);
+    // 64 warps per SM, 16 independent chains each; about 130 ms per timed
+    // launch at the maximum clock (2 FP64 / 128 FP32 FMA lanes per SM), so the
+    // launch ramp and the clock's rise are a small part of the timed region
+    const int blocks = sms * 8;
+    stencil_status s = time_chains<double>(blocks, 1 << 14, st, &measured->cu_f64_flops);
     if (s != STENCIL_OK) return s;
-    return time_chains<float>(blocks, 1 << 13, st, &measured->cu_f32_flops);
+    return time_chains<float>(blocks, 1 << 20, st, &measured->cu_f32_flops);
 } catch (...) {
     return gbs::abi_exception("stencil_probe_peaks");
 }

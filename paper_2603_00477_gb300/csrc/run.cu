@@ -187,23 +187,40 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kNoAllocMaxDevices];
 
-// Set-up, once per device, with that device current: the device address of
-// the scratch array.
-stencil_status noalloc_scratch(void **ptr)
+// The device address of the scratch array on the current device.  Outside a
+// stream capture it is looked up again on every call (cheap), so that a
+// device reset, which loads the module afresh, cannot leave a stale address;
+// during a capture the address recorded by an earlier call on this device is
+// used (the lookup may load the module, which a capture does not allow).
+stencil_status noalloc_scratch(int dev, bool capturing, void **ptr)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "stencil_run_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return fail(STENCIL_ERR_UNSUPPORTED, "stencil_run_noalloc: device ordinal above 63");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (!capturing) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_fail(e, "stencil_run_noalloc: cudaGetSymbolAddress");
         g_noalloc_ptr[dev] = p;
+    } else if (!g_noalloc_ptr[dev]) {
+        return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: the first call on a device must come before "
+                                             "any stream capture");
     }
     *ptr = g_noalloc_ptr[dev];
+    return STENCIL_OK;
+}
+
+// in and out must be device memory of the current device (the scratch array
+// is the current device's): anything else would pair buffers of two devices.
+stencil_status noalloc_check_device(const void *buf, int dev, const char *name)
+{
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, buf);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_run_noalloc: cudaPointerGetAttributes");
+    if (a.type == cudaMemoryTypeManaged) return STENCIL_OK;
+    if (a.type != cudaMemoryTypeDevice || a.device != dev)
+        return fail(STENCIL_ERR_INVALID_ARG, std::string("stencil_run_noalloc: ") + name +
+                                                 " is not device memory of the current device");
     return STENCIL_OK;
 }
 
@@ -222,14 +239,28 @@ try {
         const char *b = (const char *)in, *c = (const char *)out;
         if (b < c + g && c < b + g) return fail(STENCIL_ERR_INVALID_ARG, "stencil_run_noalloc: in and out overlap");
     }
-    if (g > kNoAllocScratchBytes)
+    // the scratch array is only the ping-pong buffer between fused sweeps: a
+    // run of at most one sweep (steps <= t) needs none, at any grid size
+    const int64_t nsweeps = steps / p.t + (steps % p.t ? 1 : 0);
+    if (nsweeps > 1 && g > kNoAllocScratchBytes)
         return fail(STENCIL_ERR_UNSUPPORTED, "stencil_run_noalloc: the grid (" + std::to_string(g) +
                                                  " bytes with halo) exceeds the 64 MiB static scratch; "
                                                  "use stencil_run with a workspace");
-    void *scratch = nullptr;
-    stencil_status s = noalloc_scratch(&scratch);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "stencil_run_noalloc: cudaGetDevice");
+    stencil_status s = noalloc_check_device(in, dev, "in");
+    if (s == STENCIL_OK) s = noalloc_check_device(out, dev, "out");
     if (s != STENCIL_OK) return s;
-    return run_sweeps(p, in, out, scratch, kNoAllocScratchBytes, steps, (cudaStream_t)stream);
+    void *scratch = nullptr;
+    if (nsweeps > 1) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+        if (e != cudaSuccess) return cuda_fail(e, "stencil_run_noalloc: cudaStreamIsCapturing");
+        s = noalloc_scratch(dev, cap != cudaStreamCaptureStatusNone, &scratch);
+        if (s != STENCIL_OK) return s;
+    }
+    return run_sweeps(p, in, out, scratch, scratch ? kNoAllocScratchBytes : 0, steps, (cudaStream_t)stream);
 } catch (...) {
     return gbs::abi_exception("stencil_run_noalloc");
 }
