@@ -345,6 +345,38 @@ def model_leg(B, inputs, tmax=8):
     return out
 
 
+def fusion_leg(B, inputs, stream, dims=(4096, 4096), tmax=8):
+    """The paper's intensity-versus-fusion-depth measurement (Sec. 5.2, the
+    figure of measured I against t), on this engine's FP64 CUDA-core sweep:
+    for Box-2D1R and Star-2D1R and t = 1..tmax, one fused sweep of depth t over
+    a grid larger than L2, timed with CUDA events, next to the model's
+    intensity I = tK/D (Eq. 8) and predicted rate.  Each (stencil, t) launches
+    the sweep kernel twice (an untimed warm-up, then the timed launch), so an
+    ncu capture of the kernel sees 2 * 2 * tmax launches in this order; its
+    DRAM bytes and FP64 instruction counts give the measured C, M and I."""
+    import numpy as np
+    import torch
+    rows = []
+    for shape in ("box", "star"):
+        w, u = inputs.problem(shape, 2, 1, dims, seed=21, dtype=np.float64)
+        x = torch.from_numpy(u).cuda()
+        y = torch.empty_like(x)
+        for t in range(1, tmax + 1):
+            plan = B.Plan(shape, 2, 1, w, "f64", dims, t)
+            plan.set_option("path", "cuda_core")
+            info = plan.info()
+            sec = _time_runs(lambda: plan.run(x, y, t), stream, reps=1, warm=1)
+            rows.append({"stencil": _stencil_name(shape, 2, 1), "t": t, "K": info["K"],
+                         "tile": info["tile"], "gstencils": math.prod(dims) * t / sec / 1e9,
+                         "sweep_ms": sec * 1e3, "model_intensity": info["intensity"],
+                         "model_gstencils": info["predicted_gstencils"],
+                         "model_memory_bound": bool(info["memory_bound"])})
+            plan.close()
+        del x, y
+        torch.cuda.empty_cache()
+    return {"workload": f"FP64 {'x'.join(map(str, dims))}, one fused sweep of depth t per row", "rows": rows}
+
+
 def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
     """Box-2D2R FP32 16384^2 (sine-mode field): plain FP32 on CUDA cores
     against the tensor-core TF32, TF32x3 and BF16x3 forms and the sparse TF32
@@ -539,7 +571,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and batched legs")
     ap.add_argument("--dims", default=None, help="override the interior extents (profiling), e.g. 6144,6144")
     ap.add_argument("--run-steps", type=int, default=None, help="override the steps per run (profiling)")
-    ap.add_argument("--leg", default="main", choices=["main", "mixed", "batched", "model"],
+    ap.add_argument("--leg", default="main", choices=["main", "mixed", "batched", "model", "fusion"],
                     help="run only the mixed-precision or the batched leg, or the host-only model "
                          "classification, and print its JSON")
     ap.add_argument("--batch-grids", type=int, default=512, help="batched leg: the first N grids (profiling)")
@@ -586,6 +618,8 @@ def main():
         stream = torch.cuda.current_stream()
         if args.leg == "mixed":
             out = mixed_precision_leg(B, inputs, stream)
+        elif args.leg == "fusion":
+            out = fusion_leg(B, inputs, stream)
         else:
             out = batched_leg(B, inputs, stream, ngrids=args.batch_grids)
         if rank == 0:
