@@ -81,14 +81,21 @@ typedef enum {
 /* Arithmetic of the products.  NATIVE: the grid's own type (FP64 grids:
  * FP64 FMA or FP64 MMA; FP32 grids: FP32 FMA).  TF32: one TF32 product with
  * FP32 accumulation.  TF32X3 / BF16X3: operands split into hi + lo parts,
- * three products (hi*hi + hi*lo + lo*hi) accumulated in FP32.  ANY: the
- * dispatcher may pick any form the grid type allows. */
+ * three products (hi*hi + hi*lo + lo*hi) accumulated in FP32.  OZAKI (FP64
+ * grids, tensor-core path): FP64 by exact splitting (the Ozaki scheme; no
+ * counterpart in the paper) -- every input tile and the composite weights
+ * are cut into S balanced 9- or 8-bit integer digits (S = 6 or 7; 53+
+ * significant bits), the S(S+1)/2 digit products of each level run on the
+ * FP16 tensor cores with exact FP32 sums, and the levels are recombined in
+ * 64-bit integers: FP64 accuracy (a few units of 2^-53 per sweep,
+ * normwise).  ANY: the dispatcher may pick any form the grid type allows. */
 typedef enum {
     STENCIL_PREC_NATIVE = 0,
     STENCIL_PREC_TF32 = 1,
     STENCIL_PREC_TF32X3 = 2,
     STENCIL_PREC_BF16X3 = 3,
-    STENCIL_PREC_ANY = 4
+    STENCIL_PREC_ANY = 4,
+    STENCIL_PREC_OZAKI = 5
 } stencil_precision;
 
 /* Peak rates the model uses (bytes/s and FLOP/s).  Table 1 of the paper:
@@ -182,7 +189,10 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
  * 3.2.3 tensor cores, Sec. 4.3 sparse tensor cores; the split-precision forms
  * have no counterpart in the paper).  Keys and values:
  *   "path"      auto | cuda_core | tensor_core | sparse_tensor_core
- *   "precision" native | tf32 | tf32x3 | bf16x3 | any
+ *   "precision" native | tf32 | tf32x3 | bf16x3 | ozaki | any   (FP32 grids:
+ *               native, tf32, tf32x3, bf16x3, any; FP64 grids: native, ozaki,
+ *               any.  ozaki runs on the tensor-core path only, 2-D, fused
+ *               radius t*r <= 8 with 9-bit digits, <= 6 with 8-bit digits)
  *   "t"         0 (model) or 1..16
  *   "tile"      "TYxTX" (2-D) or "TZxTYxTX" (3-D) output tile, "0" = default
  *   "debug_unmet_wait"  0 | 1: test hook; 1 makes every tensor-core CTA first

@@ -54,6 +54,14 @@ struct TcGeometry {
 };
 TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int precision, int path);
 
+// ---- FP64 by exact splitting (k_split.cu) ----
+// Digit slices S (6 or 7) of the plan's composite kernel at depth t for
+// which every product level sums exactly in FP32; 0 if none (or 2-D FP64
+// with t*r <= 8 does not hold).  Host only.
+int split_slices(const struct Plan &p, int t);
+// Output column blocks of 16 per tile that fit in shared memory (0: none).
+int split_nacc(int R, int S);
+
 // ---- plan ----
 struct Plan {
     Pattern pat;

@@ -788,7 +788,9 @@ stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, 
 {
     if (p.pat.d != 2) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: 2-D grids only");
     stencil_status s;
-    if (p.dtype == STENCIL_F64) {
+    if (p.dtype == STENCIL_F64 && p.precision == STENCIL_PREC_OZAKI) {
+        return launch_split_sweep(p, in, out, t, st);  // includes the band sweep
+    } else if (p.dtype == STENCIL_F64) {
         s = launch_dmma2d(p, in, out, t, st);
     } else {
         switch (p.precision) {
@@ -809,7 +811,10 @@ stencil_status read_device_error(int *flag)
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
     if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-    *flag = v;
+    int vs = 0;
+    stencil_status s = read_split_error(&vs);
+    if (s != STENCIL_OK) return s;
+    *flag = v | vs;
     return STENCIL_OK;
 }
 

@@ -23,6 +23,13 @@ stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, 
 // (mma.sp TF32), followed by the band sweep if t > 1.
 stencil_status launch_sptc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
 
+// One fused sweep of depth t of an FP64 grid on the FP16 tensor cores by
+// exact splitting (k_split.cu), followed by the band sweep if t > 1.
+stencil_status launch_split_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
+
+// Read and clear the split kernel's own error word (part of read_device_error).
+stencil_status read_split_error(int *flag);
+
 // Read and clear the device error word the tensor-core kernels set when a
 // bounded wait runs out (1 = timed out).
 stencil_status read_device_error(int *flag);

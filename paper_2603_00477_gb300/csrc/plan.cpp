@@ -159,7 +159,10 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
 {
     TcGeometry g;
     g.n_tile = 8;
-    if (dtype == STENCIL_F64) g.k_inst = 4;                    // FP64 MMA m8n8k4
+    if (dtype == STENCIL_F64 && precision == STENCIL_PREC_OZAKI) {
+        g.n_tile = 16;  // tcgen05 kind::f16: 16 output columns per digit block, K = 16
+        g.k_inst = 16;
+    } else if (dtype == STENCIL_F64) g.k_inst = 4;             // FP64 MMA m8n8k4
     else if (precision == STENCIL_PREC_BF16X3) g.k_inst = 16;  // kind::f16 K = 16
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
@@ -178,7 +181,7 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
         TcLines L = tc_lines_2d(shape, r, t, g.n_tile, g.k_inst);
         g.kext = L.kext;
         g.sparsity = L.sparsity();
-        g.available = t * r <= 12;
+        g.available = t * r <= (precision == STENCIL_PREC_OZAKI ? 8 : 12);
         return g;
     }
     // 3-D (model only): every (plane, row) line of the composite issues its
@@ -206,7 +209,7 @@ bool tc_supported(const Plan &p, int precision, int path)
     if (path == STENCIL_PATH_SPARSE_TENSOR_CORE)  // mma.sp TF32 (1:2 per pair of K)
         return p.dtype == STENCIL_F32 && precision == STENCIL_PREC_TF32;
     if (path != STENCIL_PATH_TENSOR_CORE) return false;
-    if (p.dtype == STENCIL_F64) return precision == STENCIL_PREC_NATIVE;
+    if (p.dtype == STENCIL_F64) return precision == STENCIL_PREC_NATIVE || precision == STENCIL_PREC_OZAKI;
     return precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3;
 }
 
@@ -214,13 +217,17 @@ static double tc_peak(const Plan &p, int precision, int path)
 {
     const stencil_peaks &pk = peaks();
     const bool sparse = path == STENCIL_PATH_SPARSE_TENSOR_CORE;
+    if (p.dtype == STENCIL_F64 && precision == STENCIL_PREC_OZAKI) return pk.tc_bf16_flops;  // FP16 = BF16 rate
     if (p.dtype == STENCIL_F64) return pk.tc_f64_flops;
     if (precision == STENCIL_PREC_BF16X3) return sparse ? pk.sptc_bf16_flops : pk.tc_bf16_flops;
     return sparse ? pk.sptc_tf32_flops : pk.tc_tf32_flops;
 }
 
-static double beta_of(int precision)
+// Products issued per useful product: 3 for the hi/lo forms; S(S+1)/2 digit
+// products (levels i + j < S of S slices each) for the exact-split FP64 form.
+static double beta_of(int precision, int slices = 0)
 {
+    if (precision == STENCIL_PREC_OZAKI) return slices * (slices + 1) / 2.0;
     return (precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3) ? 3.0 : 1.0;
 }
 
@@ -263,6 +270,8 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
             precs.push_back(STENCIL_PREC_TF32);
             precs.push_back(STENCIL_PREC_TF32X3);
             precs.push_back(STENCIL_PREC_BF16X3);
+        } else {
+            precs.push_back(STENCIL_PREC_OZAKI);
         }
     } else {
         precs.push_back(p->req_precision);
@@ -288,6 +297,12 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
             int t_hi = p->req_t ? p->req_t : max_fused_t(*p, path);
             for (int t = t_lo; t <= t_hi; t++) {
                 if (path != STENCIL_PATH_CUDA_CORE && t * r > 12) continue;
+                int slices = 0;
+                if (prec == STENCIL_PREC_OZAKI) {
+                    if (path != STENCIL_PATH_TENSOR_CORE) continue;
+                    slices = split_slices(*p, t);
+                    if (slices == 0 || split_nacc(t * r, slices) == 0) continue;
+                }
                 Cand c{path, prec, t, 0.0, {1, 1, 1}};
                 if (path == STENCIL_PATH_CUDA_CORE) {
                     if (p->req_tile[0] || p->req_tile[1] || p->req_tile[2]) {
@@ -305,8 +320,12 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                     c.tile[1] = p->dtype == STENCIL_F64 ? 64 : 128;
                     c.tile[2] = p->dtype == STENCIL_F64 ? 64 : (prec == STENCIL_PREC_TF32 ? 64 : (prec == STENCIL_PREC_TF32X3 ? 32 : 64));
                     if (path == STENCIL_PATH_SPARSE_TENSOR_CORE) c.tile[2] = 64;
+                    if (prec == STENCIL_PREC_OZAKI) {
+                        c.tile[1] = 128;
+                        c.tile[2] = 16 * split_nacc(t * r, slices);
+                    }
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
-                    ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec), P_cu,
+                    ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec, slices), P_cu,
                                             tc_peak(*p, prec, path), B);
                     c.gst = m.gst_tc;
                 }
@@ -339,7 +358,8 @@ stencil_status dispatch(Plan *p)
             continue;
         }
         auto key = [](const Cand &x) {
-            return std::make_tuple(x.path == STENCIL_PATH_CUDA_CORE ? 0 : 1, x.t, beta_of(x.prec));
+            return std::make_tuple(x.path == STENCIL_PATH_CUDA_CORE ? 0 : 1, x.t,
+                                   x.prec == STENCIL_PREC_OZAKI ? 100.0 : beta_of(x.prec));
         };
         if (key(c) < key(*pick)) pick = &c;
     }
@@ -356,11 +376,13 @@ stencil_status dispatch(Plan *p)
     in.precision = p->precision;
     in.t = p->t;
     for (int i = 0; i < 3; i++) in.tile[i] = p->tile[i];
-    const int tc_prec = p->dtype == STENCIL_F64 ? STENCIL_PREC_NATIVE
+    const int tc_prec = p->dtype == STENCIL_F64 ? (p->precision == STENCIL_PREC_OZAKI ? STENCIL_PREC_OZAKI
+                                                                                      : STENCIL_PREC_NATIVE)
                         : (p->precision == STENCIL_PREC_NATIVE ? STENCIL_PREC_TF32 : p->precision);
     const int tc_path = p->path == STENCIL_PATH_CUDA_CORE ? STENCIL_PATH_TENSOR_CORE : p->path;
+    const int slices = tc_prec == STENCIL_PREC_OZAKI ? split_slices(*p, p->t) : 0;
     TcGeometry g = tc_geometry(shape, d, r, p->t, p->dtype, tc_prec, tc_path);
-    ModelOut m = model_eval(shape, d, r, p->t, D, g.sparsity, beta_of(tc_prec), P_cu,
+    ModelOut m = model_eval(shape, d, r, p->t, D, g.sparsity, beta_of(tc_prec, slices), P_cu,
                             tc_peak(*p, tc_prec, tc_path), B);
     in.K = m.K;
     in.K_fused = m.K_fused;
@@ -378,7 +400,7 @@ stencil_status dispatch(Plan *p)
     } else {
         in.alpha = m.alpha;
         in.sparsity = g.sparsity;
-        in.beta = beta_of(tc_prec);
+        in.beta = beta_of(tc_prec, slices);
         in.intensity = m.I_tc;
         in.ridge = m.ridge_tc;
         in.memory_bound = m.I_tc < m.ridge_tc;
@@ -468,11 +490,14 @@ try {
         else if (v == "tf32") trial.req_precision = STENCIL_PREC_TF32;
         else if (v == "tf32x3") trial.req_precision = STENCIL_PREC_TF32X3;
         else if (v == "bf16x3") trial.req_precision = STENCIL_PREC_BF16X3;
+        else if (v == "ozaki") trial.req_precision = STENCIL_PREC_OZAKI;
         else if (v == "any") trial.req_precision = STENCIL_PREC_ANY;
-        else return fail(STENCIL_ERR_INVALID_ARG, "precision must be native|tf32|tf32x3|bf16x3|any");
+        else return fail(STENCIL_ERR_INVALID_ARG, "precision must be native|tf32|tf32x3|bf16x3|ozaki|any");
         if (trial.dtype == STENCIL_F64 && trial.req_precision != STENCIL_PREC_NATIVE &&
-            trial.req_precision != STENCIL_PREC_ANY)
-            return fail(STENCIL_ERR_INVALID_ARG, "FP64 grids take precision native or any");
+            trial.req_precision != STENCIL_PREC_ANY && trial.req_precision != STENCIL_PREC_OZAKI)
+            return fail(STENCIL_ERR_INVALID_ARG, "FP64 grids take precision native, ozaki or any");
+        if (trial.dtype == STENCIL_F32 && trial.req_precision == STENCIL_PREC_OZAKI)
+            return fail(STENCIL_ERR_INVALID_ARG, "precision ozaki is for FP64 grids");
     } else if (k == "t") {
         long t = 0;
         if (!parse_int(value, &t) || t < 0 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "t must be 0..16");
@@ -551,9 +576,10 @@ try {
     if (!plan || !layout) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_tc_layout: null argument");
     const Plan &p = plan->p;
     if (t < 1 || t > kMaxT) return fail(STENCIL_ERR_INVALID_ARG, "stencil_plan_tc_layout: t must be 1..16");
-    int prec = p.dtype == STENCIL_F64 ? STENCIL_PREC_NATIVE : p.precision;
+    int prec = p.dtype == STENCIL_F64 ? (p.precision == STENCIL_PREC_OZAKI ? STENCIL_PREC_OZAKI : STENCIL_PREC_NATIVE)
+                                      : p.precision;
     if (p.dtype == STENCIL_F32 && prec == STENCIL_PREC_NATIVE) prec = STENCIL_PREC_TF32;
-    if (!tc_supported(p, prec, STENCIL_PATH_TENSOR_CORE) || t * p.pat.r > 12)
+    if (!tc_supported(p, prec, STENCIL_PATH_TENSOR_CORE) || t * p.pat.r > (prec == STENCIL_PREC_OZAKI ? 8 : 12))
         return fail(STENCIL_ERR_UNSUPPORTED, "stencil_plan_tc_layout: no tensor-core kernel for this plan and t");
     TcGeometry g = tc_geometry(p.pat.shape, p.pat.d, p.pat.r, t, p.dtype, prec, STENCIL_PATH_TENSOR_CORE);
     TcLines L = tc_lines_2d(p.pat.shape, p.pat.r, t, g.n_tile, g.k_inst);
