@@ -237,7 +237,7 @@ def kernel_name(info: dict, d: int, dtype: str) -> str:
     if info["path"] == 3:
         return "sptc2d_sweep"
     if dtype == "f64":
-        return "dmma2d_sweep"
+        return "tc2d_split" if info["precision_name"] == "ozaki" else "dmma2d_sweep"
     return "tc2d_sweep" if info["precision_name"] == "bf16x3" else "tc2d_ws"
 
 
@@ -464,6 +464,67 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
             "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests)",
             "plain_fp32_cuda_core_gstencils": plain, "best": best, "crossover": crossover, "rows": rows,
             "errors": errors}
+
+
+def split_fp64_leg(B, cfg, w, u, x, y_plain, plain_gstencils, stream, reps):
+    """FP64 on the FP16 tensor cores by exact splitting (precision "ozaki")
+    on the headline FP64 workload, next to the plain FP64 path already timed:
+    point-updates/s over `reps` runs (CUDA events), the normwise error against
+    the plain path's result on the whole grid and against the CPU oracle on
+    two sampled boxes, and the tensor-core work of its kernel (tc2d_split):
+    useful FP64 FLOP (2K per point-step) and issued FP16 MMA FLOP (the model's
+    beta/S times the useful work, beta = S(S+1)/2 digit products)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    dims, steps = cfg["dims"], cfg["steps"]
+    if cfg["d"] != 2:
+        return None
+    plan = B.Plan(cfg["shape"], 2, cfg["r"], w, "f64", dims, 0)
+    try:
+        plan.set_option("precision", "ozaki")
+        plan.set_option("path", "tensor_core")
+    except B.StencilError as e:
+        plan.close()
+        return {"unavailable": str(e)}
+    info = plan.info()
+    plan.ensure_workspace(x.device)
+    z = torch.empty_like(x)
+    sec = _time_runs(lambda: plan.run(x, z, steps), stream, reps=reps, warm=1)
+    pts = math.prod(dims)
+    value = pts * steps / sec / 1e9
+    r = cfg["r"]
+    inner = (slice(r, -r), slice(r, -r))
+    err_plain = float((z[inner] - y_plain[inner]).abs().max() / y_plain[inner].abs().max())
+    samples = [((0, 0), (4, 4)), ((dims[0] // 2, dims[1] // 2), (dims[0] // 2 + 3, dims[1] // 2 + 5))]
+    got, ref = [], []
+    for lo, hi in samples:
+        ref.append(oracle.run_region(cfg["shape"], 2, r, w, dims, u, steps, lo, hi).ravel())
+        got.append(z[lo[0] + r:hi[0] + r, lo[1] + r:hi[1] + r].cpu().numpy().ravel())
+    err_oracle = oracle.rel_linf(np.concatenate(got), np.concatenate(ref))
+    t = info["t"]
+    nsweeps = steps // t + (1 if steps % t else 0)
+    launch_s = sec / nsweeps
+    useful = pts * 2 * info["K"] * (steps / nsweeps)  # FLOP of one sweep (t steps)
+    issued = useful * info["alpha"] * info["beta"] / info["sparsity"]
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 0.0)) or 0.0)
+    S = int(round((math.sqrt(1 + 8 * info["beta"]) - 1) / 2))
+    plan.close()
+    del z
+    torch.cuda.empty_cache()
+    return {"workload": config_json("", cfg)["workload"], "path": "tensor_core", "precision": "ozaki",
+            "t": t, "digit_slices": S, "products_per_useful_product": info["beta"], "sparsity": info["sparsity"],
+            "gstencils": value, "vs_plain_fp64": value / plain_gstencils if plain_gstencils else None,
+            "model_gstencils": info["predicted_gstencils"],
+            "rel_linf_vs_plain_fp64_gpu": err_plain, "rel_linf_vs_oracle_sampled": err_oracle,
+            "oracle_samples": [[list(lo), list(hi)] for lo, hi in samples],
+            "kernel": {"name": "tc2d_split", "avg_launch_ms": launch_s * 1e3,
+                       "useful_fp64_tflops": useful / launch_s / 1e12,
+                       "issued_fp16_tflops": issued / launch_s / 1e12, "peak_tflops": peak,
+                       "peak_source": f"bf16_tflops_sustained of {src} peaks (FP16 and BF16 share the dense rate)",
+                       "issued_frac": issued / launch_s / 1e12 / peak if peak else None}}
 
 
 def batched_leg(B, inputs, stream, steps=20, ngrids=512):
@@ -713,6 +774,23 @@ def main():
     if not args.no_e2e:
         h_in = torch.from_numpy(u).pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
+
+        def copy_rates():
+            # the copy rates of the pinned buffers alone (CUDA events on the stream)
+            d_buf = torch.empty(tuple(h_in.shape), dtype=h_in.dtype, device=x.device)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            d_buf.copy_(h_in, non_blocking=True)
+            ev[1].record(stream)
+            h_out.copy_(d_buf, non_blocking=True)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            nb = h_in.numel() * h_in.element_size()
+            del d_buf
+            return (nb / (max(ev[0].elapsed_time(ev[1]), 1e-6) / 1e3) / 1e9,
+                    nb / (max(ev[1].elapsed_time(ev[2]), 1e-6) / 1e3) / 1e9)
+
+        before = copy_rates()
         plan.run_host(h_in, h_out, steps)  # warm (workspace of three grids)
         torch.cuda.synchronize()
         barrier()
@@ -727,31 +805,36 @@ def main():
         e2e = {"value": whole_job_rate(world, pts, steps, args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "api": "stencil_run_host (pinned host buffers)", "clocks": e2e_clocks.summary()}
-        # the copy rates of the same pinned buffers alone (CUDA events), which
-        # split the end-to-end time into copies and compute
-        d_buf = torch.empty(tuple(h_in.shape), dtype=h_in.dtype, device=x.device)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record(stream)
-        d_buf.copy_(h_in, non_blocking=True)
-        ev[1].record(stream)
-        h_out.copy_(d_buf, non_blocking=True)
-        ev[2].record(stream)
-        torch.cuda.synchronize()
-        e2e["h2d_gbs"] = nbytes / (max(ev[0].elapsed_time(ev[1]), 1e-6) / 1e3) / 1e9
-        e2e["d2h_gbs"] = nbytes / (max(ev[1].elapsed_time(ev[2]), 1e-6) / 1e3) / 1e9
-        del h_in, h_out, d_buf
+        # the copy rates of the same pinned buffers alone, before and after the
+        # timed region: they split the end-to-end time into copies and compute
+        e2e["h2d_gbs"], e2e["d2h_gbs"] = copy_rates()
+        e2e["h2d_gbs_before"], e2e["d2h_gbs_before"] = before
+        del h_in, h_out
         plan._ws = None
         torch.cuda.empty_cache()
         plan.ensure_workspace(x.device)
+
+    # FP64 by exact splitting on the tensor cores, against the plain result in y
+    split_leg = None
+    if not args.no_extras and rank == 0 and cfg["dtype"] == "f64" and cfg["d"] == 2 and \
+            info["precision_name"] != "ozaki":
+        import oracle
+        oracle.build()
+        split_leg = split_fp64_leg(B, cfg, w, u, x, y, value / world, stream, args.steps)
 
     # per-(path, t) sweep of the headline workload next to the model's prediction
     sweep = None
     if not args.no_sweep and rank == 0:
         sweep = []
-        for path in ("cuda_core", "tensor_core"):
+        forms = [("cuda_core", None), ("tensor_core", None)]
+        if cfg["dtype"] == "f64":
+            forms.append(("tensor_core", "ozaki"))
+        for path, prec in forms:
             for tt_ in (1, 2, 3, 4):
                 try:
                     p2 = B.Plan(cfg["shape"], cfg["d"], cfg["r"], w, cfg["dtype"], cfg["dims"], tt_)
+                    if prec:
+                        p2.set_option("precision", prec)
                     p2.set_option("path", path)
                 except B.StencilError:
                     continue
@@ -765,13 +848,16 @@ def main():
                 b.record(stream)
                 torch.cuda.synchronize()
                 i2 = p2.info()
-                sweep.append({"path": path, "t": tt_, "gstencils": pts * steps / (a.elapsed_time(b) / 1e3) / 1e9,
+                sweep.append({"path": path, "precision": i2["precision_name"], "t": tt_,
+                              "gstencils": pts * steps / (a.elapsed_time(b) / 1e3) / 1e9,
                               "model_gstencils": i2["predicted_gstencils"], "alpha": i2["alpha"],
-                              "sparsity": i2["sparsity"]})
+                              "sparsity": i2["sparsity"], "beta": i2["beta"]})
                 p2._ws = None
                 p2.close()
 
     extras = {}
+    if split_leg is not None:
+        extras["mixed_precision_fp64"] = split_leg
     if not args.no_extras and rank == 0 and args.config == DEFAULT and not args.dims:
         del x, y
         plan._ws = None

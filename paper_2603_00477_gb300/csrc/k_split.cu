@@ -35,8 +35,8 @@
 // 53 of w^(t)), rounded once: the error is a few units of 2^-53 of
 // max|u| * sum|w| per sweep (normwise), like FP64 arithmetic.
 //
-// The kernel is warp specialised and persistent (one CTA per SM, 288
-// threads): warp 8 issues the MMAs; warps 0-7 load the next tile's FP64
+// The kernel is warp specialised and persistent (one CTA per SM, 544
+// threads): warp 16 issues the MMAs; warps 0-15 load the next tile's FP64
 // input into registers, reduce its exponent, cut it into digit slices in
 // shared memory (chunk-column K-major layout, the implicit im2col of k_tc.cu)
 // and drain the previous tile's accumulators (double-buffered TMEM).  Only
@@ -72,14 +72,18 @@ constexpr int kMaxLines = 2 * kMaxR + 1;
 constexpr int kMaxS = 7;  // S = 8 (7-bit digits) is only needed at fused radii whose tiles do not fit
 constexpr int TM = 128, TN = 16, KI = 16;      // MMA M, N per accumulator block, K per instruction
 constexpr int kNkb = 2;                        // K blocks per line (window 16 + 2R <= 32)
-constexpr int kWorkers = 256;                  // warps 0-7
-constexpr int kItemsPerThread = 4;             // (TM + 2R) * NCH <= 144 * 6 = 864 <= 4 * 256
+constexpr int kWorkerWarps = 16;
+constexpr int kWorkers = 32 * kWorkerWarps;    // warps 0-15; warp 16 issues the MMAs
+constexpr int kThreads = kWorkers + 32;
+constexpr int kItemsPerThread = 2;             // (TM + 2R) * NCH <= 144 * 6 = 864 <= 2 * 512
+constexpr int kHeader = 256;                   // TMEM slot, abort word, mbarriers, exponent slots
 
 struct SplitParams {
     short wd[kMaxS][kMaxLines * kMaxLines];  // weight digits b_j of w^(t), (2R+1)^2 row-major
     unsigned char kb_lo[kMaxLines], kb_hi[kMaxLines];
     int R, rh, band, hs, nch;
     int scale0;        // b(S-1) + D + E_w - 2 NB - 1022: the result scale is 2^(scale0 + emax)
+    int vec16;         // rows start on 16-byte boundaries and X0 - R is even: 16-byte loads
     int debug_unmet;   // test hook: a wait on an mbarrier phase that never completes
     int64_t Ey, Ex;
 };
@@ -126,18 +130,31 @@ __device__ __forceinline__ long long fixed_point(unsigned long long X, int emax)
 // The S balanced b-bit digits of V (top first), each as the FP16 bit pattern
 // of 1536 + digit (exact: 1536 +- 2^(b-1) lies in [1024, 2048), where FP16
 // steps by 1); 1536 is subtracted after packing two digits into a half2.
+// V is split at 3b bits into a non-negative low word (three digits, then a
+// carry of 0 or 1) and a signed high word (the rest), so every step is a
+// 32-bit operation: |V| <= 2^(S b - 1) leaves |V >> 3b| < 2^31.
 template <int S>
 __device__ __forceinline__ void digits16(long long V, unsigned short (&h)[S])
 {
     constexpr int b = Digits<S>::b;
     constexpr int half = 1 << (b - 1), mask = (1 << b) - 1;
+    constexpr int LO = 3;  // digits in the low word
+    int lo = (int)((unsigned long long)V & ((1ull << (LO * b)) - 1));
+    int hi = (int)(V >> (LO * b));
 #pragma unroll
-    for (int i = S - 1; i >= 1; --i) {
-        const int d = (((int)V & mask) ^ half) - half;  // in [-2^(b-1), 2^(b-1))
+    for (int i = S - 1; i >= S - LO; --i) {
+        const int d = ((lo & mask) ^ half) - half;  // in [-2^(b-1), 2^(b-1))
         h[i] = (unsigned short)(0x6600 + d);
-        V = (V - d) >> b;
+        lo = (lo - d) >> b;
     }
-    h[0] = (unsigned short)(0x6600 + (int)V);  // |top digit| <= 2^(b-1)
+    hi += lo;  // the carry out of the low word
+#pragma unroll
+    for (int i = S - LO - 1; i >= 1; --i) {
+        const int d = ((hi & mask) ^ half) - half;
+        h[i] = (unsigned short)(0x6600 + d);
+        hi = (hi - d) >> b;
+    }
+    h[0] = (unsigned short)(0x6600 + hi);  // |top digit| <= 2^(b-1)
 }
 
 __device__ __forceinline__ uint32_t hsub1536(uint32_t packed)
@@ -148,7 +165,7 @@ __device__ __forceinline__ uint32_t hsub1536(uint32_t packed)
 }
 
 template <int S, int NACC>
-__global__ void __launch_bounds__(288, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     tc2d_split(const double *__restrict__ in, double *__restrict__ out, const __grid_constant__ SplitParams p,
                int ntiles, int ntx)
 {
@@ -166,12 +183,13 @@ __global__ void __launch_bounds__(288, 1)
     uint64_t *done = reinterpret_cast<uint64_t *>(smem + 32);   // [2]
     uint64_t *freeb = reinterpret_cast<uint64_t *>(smem + 48);  // [2]
     uint64_t *emaxb = reinterpret_cast<uint64_t *>(smem + 64);  // [2]: the tile exponent is reduced
-    int *wmax = reinterpret_cast<int *>(smem + 80);             // [2][8]
+    int *wmax = reinterpret_cast<int *>(smem + 80);             // [2][kWorkerWarps], bytes 80..207
+    static_assert(80 + 2 * kWorkerWarps * sizeof(int) <= kHeader, "the header holds the barriers and exponents");
     const int R = p.R, HS = p.hs, NCH = p.nch;
     const int lines = 2 * R + 1;
     const uint32_t slice_bytes = (uint32_t)NCH * HS * 16;
     const uint32_t a_bytes = slice_bytes * S;
-    unsigned char *Bm = smem + 128;
+    unsigned char *Bm = smem + kHeader;
     unsigned char *A[2] = {Bm + (size_t)lines * kNkb * kBlk, Bm + (size_t)lines * kNkb * kBlk + a_bytes};
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t Ey = p.Ey, Ex = p.Ex, rh = p.rh;
@@ -224,7 +242,7 @@ __global__ void __launch_bounds__(288, 1)
         *X0 = rh + (int64_t)(id % ntx) * TX;
     };
 
-    if (warp == 8) {
+    if (warp == kWorkerWarps) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t lbo_a = (uint32_t)HS * 16;
@@ -263,7 +281,7 @@ __global__ void __launch_bounds__(288, 1)
         }
         __syncwarp();
     } else {
-        // -------- loaders / digit cutters and epilogue (warps 0-7) --------
+        // -------- loaders / digit cutters and epilogue (warps 0-15) --------
         const int rows = TM + 2 * R;
         const int nitems = rows * NCH;
         double v[kItemsPerThread][8];
@@ -277,6 +295,17 @@ __global__ void __launch_bounds__(288, 1)
                 const int64_t gy = Y0 - R + row, gx0 = X0 - R + 8 * c;
                 const bool rowok = it < nitems && gy >= 0 && gy < Ey;
                 const double *src = in + (rowok ? gy : 0) * Ex;
+                if (p.vec16 && rowok && gx0 >= 0 && gx0 + 8 <= Ex) {
+                    // the eight values lie in the row and start on a 16-byte boundary
+                    const double2 *s2 = reinterpret_cast<const double2 *>(src + gx0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const double2 d2 = __ldg(s2 + e);
+                        v[j][2 * e] = d2.x;
+                        v[j][2 * e + 1] = d2.y;
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int64_t gx = gx0 + e;
@@ -284,7 +313,7 @@ __global__ void __launch_bounds__(288, 1)
                 }
             }
         };
-        // largest biased exponent of the staged tile k (>= 1) over the 256
+        // largest biased exponent of the staged tile k (>= 1) over the
         // workers: per-warp maxima in shared memory, exchanged through an
         // mbarrier with a bounded wait (-1: the wait gave up)
         auto tile_emax = [&](int k) -> int {
@@ -296,13 +325,13 @@ __global__ void __launch_bounds__(288, 1)
                 for (int e = 0; e < 8; ++e)
                     mx = max(mx, (int)((__double_as_longlong(v[j][e]) >> 52) & 0x7FF));
             mx = __reduce_max_sync(0xffffffffu, (unsigned)mx);
-            if (lane == 0) wmax[slot * 8 + warp] = mx;
+            if (lane == 0) wmax[slot * kWorkerWarps + warp] = mx;
             __syncwarp();
             mbar_arrive(&emaxb[slot]);
             if (!bounded_wait(&emaxb[slot], (k >> 1) & 1, kWaitCycles)) return -1;
-            int m = wmax[slot * 8];
+            int m = wmax[slot * kWorkerWarps];
 #pragma unroll
-            for (int w = 1; w < 8; ++w) m = max(m, wmax[slot * 8 + w]);
+            for (int w = 1; w < kWorkerWarps; ++w) m = max(m, wmax[slot * kWorkerWarps + w]);
             return m;
         };
         auto cut = [&](unsigned char *Abuf, int emax) {
@@ -336,17 +365,36 @@ __global__ void __launch_bounds__(288, 1)
             const bool rowok = iy < ny && iy >= p.band && ny - 1 - iy >= p.band;
             const uint32_t lane_base = tmem + bf * kSet + ((uint32_t)((warp & 3) * 32) << 16);
             const bool nan_tile = emax == 0x7FF;
-            // 2^(scale0 + emax) as a double (inputs of normal magnitude keep it normal)
-            int sc = p.scale0 + emax;
-            sc = max(-1022, min(1023, sc));
-            const double scale = __longlong_as_double((long long)(sc + 1023) << 52);
-            for (int g = warp >> 2; g < 2 * NACC; g += 2) {
+            // the result is T * 2^sc.  (double)T has a biased exponent in
+            // [1023, 1085] (1 <= |T| < 2^63), so adding sc to the exponent
+            // field scales exactly when that stays a normal number; otherwise
+            // two multiplications by powers of two do it
+            const int sc = p.scale0 + emax;
+            const bool exp_add = sc >= 1 - 1023 && sc <= 2046 - 1085;
+            const int sc1 = sc / 2, sc2 = sc - sc1;
+            const double s1 = __longlong_as_double((long long)(max(-1022, min(1023, sc1)) + 1023) << 52);
+            const double s2 = __longlong_as_double((long long)(max(-1022, min(1023, sc2)) + 1023) << 52);
+            const long long sc_bits = (long long)sc << 52;
+            for (int g = warp >> 2; g < 2 * NACC; g += kWorkerWarps / 4) {
                 const int q = g >> 1, h = g & 1;
-                uint32_t acc[S][8];
-                __syncwarp();  // tcgen05.ld is warp-collective
+                // T = sum_L S_L 2^(b(S-1-L) - D), one level at a time
+                long long T[8];
 #pragma unroll
-                for (int L = 0; L < S; ++L) tmem_ld_32x32b_x8(lane_base + q * TN * S + TN * L + 8 * h, acc[L]);
-                tmem_ld_wait();
+                for (int c = 0; c < 8; ++c) T[c] = 0;
+#pragma unroll
+                for (int L = 0; L < S; ++L) {
+                    uint32_t acc[8];
+                    __syncwarp();  // tcgen05.ld is warp-collective
+                    tmem_ld_32x32b_x8(lane_base + q * TN * S + TN * L + 8 * h, acc);
+                    tmem_ld_wait();
+                    const int sh = b * (S - 1 - L) - D;  // compile-time after unrolling
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const long long sL = (long long)__float2int_rn(__uint_as_float(acc[c]));
+                        if (sh >= 0) T[c] += sL * (1ll << sh);
+                        else T[c] += (sL + (1ll << (-sh - 1))) >> (-sh);
+                    }
+                }
                 if (!rowok) continue;
                 const int64_t gx0 = X0 + q * TN + 8 * h;
                 double *dst = out + gy * Ex;
@@ -354,15 +402,10 @@ __global__ void __launch_bounds__(288, 1)
                 for (int c = 0; c < 8; ++c) {
                     const int64_t gx = gx0 + c, ix = gx - rh;
                     if (ix >= nx || ix < p.band || nx - 1 - ix < p.band) continue;
-                    long long T = 0;
-#pragma unroll
-                    for (int L = 0; L < S; ++L) {
-                        const long long sL = (long long)__float2int_rn(__uint_as_float(acc[L][c]));
-                        const int sh = b * (S - 1 - L) - D;  // compile-time after unrolling
-                        if (sh >= 0) T += sL * (1ll << sh);
-                        else T += (sL + (1ll << (-sh - 1))) >> (-sh);
-                    }
-                    dst[gx] = nan_tile ? __longlong_as_double(0x7FF8000000000000ll) : (double)T * scale;
+                    const double r = (double)T[c];
+                    const double v = exp_add ? (T[c] ? __longlong_as_double(__double_as_longlong(r) + sc_bits) : 0.0)
+                                             : r * s1 * s2;
+                    dst[gx] = nan_tile ? __longlong_as_double(0x7FF8000000000000ll) : v;
                 }
             }
         };
@@ -528,7 +571,7 @@ int split_nacc(int R, int S)
         const int nch = 2 * nacc + 2;
         const size_t a_bytes = (size_t)S * nch * hs * 16;
         const size_t b_bytes = (size_t)(2 * R + 1) * split::kNkb * 2 * S * 256;
-        if (128 + b_bytes + 2 * a_bytes <= 227 * 1024) return nacc;
+        if (split::kHeader + b_bytes + 2 * a_bytes <= 227 * 1024) return nacc;
     }
     return 0;
 }
@@ -544,7 +587,7 @@ stencil_status launch_split_n(const Plan &p, const split::SplitParams &sp, const
     tp.nch = 2 * NACC + 2;
     const size_t a_bytes = (size_t)S * tp.nch * tp.hs * 16;
     const size_t b_bytes = (size_t)(2 * tp.R + 1) * kNkb * 2 * S * 256;
-    const size_t smem = 128 + b_bytes + 2 * a_bytes;
+    const size_t smem = kHeader + b_bytes + 2 * a_bytes;
     auto kern = tc2d_split<S, NACC>;
     stencil_status s = ensure_smem((const void *)kern, smem);
     if (s != STENCIL_OK) return s;
@@ -556,7 +599,11 @@ stencil_status launch_split_n(const Plan &p, const split::SplitParams &sp, const
     const int64_t ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
-    kern<<<grid, 288, smem, st>>>((const double *)in, (double *)out, tp, (int)ntiles, (int)ntx);
+    // staged windows start at column X0 - R = (r - R) + 32 tx: 16-byte loads
+    // when that is even, the stored rows are 16-byte multiples and `in` is
+    // 16-byte aligned
+    tp.vec16 = ((p.pat.r - tp.R) % 2 == 0) && (p.ext[2] % 2 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
+    kern<<<grid, kThreads, smem, st>>>((const double *)in, (double *)out, tp, (int)ntiles, (int)ntx);
     note_launch();
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_split launch");

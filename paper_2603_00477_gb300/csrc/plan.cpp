@@ -5,7 +5,8 @@
 // min(P S / (2K alpha beta), t B / (2D)) (Eq. 8 for CUDA cores, Eq. 12 for
 // tensor cores, Eq. 20 with the sparse peak), the CUDA-core compute term
 // being divided by the redundant work of overlapped temporal tiles (the
-// halo overlap the paper leaves out of its model).  The fastest candidate
+// halo overlap the paper leaves out of its model), and the tensor-core term
+// capped by an instruction-level roof (the MMA-shape efficiency below).  The fastest candidate
 // wins; candidates within 2 % of it are ordered CUDA cores first (no
 // redundancy), then smaller t, then fewer products.
 #include <algorithm>
@@ -231,6 +232,97 @@ static double beta_of(int precision, int slices = 0)
     return (precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3) ? 3.0 : 1.0;
 }
 
+// ---------------------------------------------------------------------------
+// MMA-shape efficiency (the eta(N) term the paper's model does not have).
+//
+// On GB300 a tcgen05.mma of M = 128 and 32 bytes of K per row costs a fixed
+// ~90 cycles from one instruction to the next in these kernels, whatever its
+// N (16..96 measured), its operand layout or its accumulator dependencies,
+// until its own arithmetic (128 N K / rate: 2048 TF32 or 4096 FP16/BF16 MACs
+// per cycle) is longer.  A sweep kernel therefore runs at
+//     cycles per output = max(MMAs per output * cost per MMA,
+//                             worker cycles per output)
+// (their sum for the synchronous BF16x3 kernel), the second term being the
+// CUDA-core work of staging, rounding or cutting the input and draining the
+// accumulators, measured per kernel at t = 1 on GB300 at 2070 MHz.  The
+// instruction roof t * SMs * clock / cycles per output caps the paper's
+// tensor-core roof (Eq. 12) for the dispatcher.
+// ---------------------------------------------------------------------------
+constexpr double kMmaCycles = 90.0;        // per tcgen05.mma, M = 128, N <= ~176
+constexpr double kWorkerTf32 = 1.30;       // tc2d_ws TF32: in-place rounding, staging, epilogue
+constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
+constexpr double kWorkerBf16x3 = 1.18;     // tc2d_sweep BF16x3 (synchronous: added to the MMAs)
+constexpr double kWorkerSplit = 4.06;      // tc2d_split: FP64 load, exponent, digit cut, recombination
+// sptc2d_sweep issues warp-level mma.sp between its staging and epilogue
+// work, so the two add: 0.92 cycles per output plus 3.15 per sparse
+// instruction of an output (fitted to Box-2D2R at t = 1..4 within 4 %)
+constexpr double kWorkerSparse = 0.92;
+constexpr double kSparseMmaCycles = 3.15;
+// cu2d_sweep FP32 (one sub-step): 2.64 thread instructions per tap and
+// output (66 for the 25 taps of Box-2D2R, ncu) issued at 72 % of the SM's
+// 128 per cycle; fused sub-steps repeat it over the overlapped tile
+constexpr double kCuF32InstrPerTap = 2.64;
+constexpr double kCuF32IssueEff = 0.72;
+
+// Instruction-level roof (point updates/s / 1e9) of a tensor-core candidate;
+// 0 when it does not apply (FP64 MMA, which the paper's model covers).
+static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
+{
+    const stencil_peaks pk = peaks();
+    const double sm_clk = pk.cu_f32_flops / 256.0;  // SMs x clock (128 FP32 FMA lanes per SM)
+    if (p.pat.d != 2 || sm_clk <= 0) return 0;
+    const int shape = p.pat.shape, r = p.pat.r;
+    double per_out = 0;
+    if (path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
+        const SpLayout L = sp_layout_2d(shape, r, t);
+        double instr = 0;
+        for (int m : L.mask) instr += __builtin_popcount((unsigned)m);
+        per_out = kWorkerSparse + instr / (16.0 * 8.0) * kSparseMmaCycles;
+    } else if (p.dtype == STENCIL_F64 && prec == STENCIL_PREC_OZAKI) {
+        const int S = split_slices(p, t);
+        if (S == 0) return 0;
+        const TcLines L = tc_lines_2d(shape, r, t, 16, 16);
+        double blocks = 0;
+        for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
+        const double mma = blocks * S / (128.0 * 16.0) * kMmaCycles;
+        per_out = std::max(mma, kWorkerSplit);
+    } else if (p.dtype == STENCIL_F32) {
+        const bool bf = prec == STENCIL_PREC_BF16X3;
+        const int n = bf ? 8 : tc_ws_ntile(shape, r, t, prec == STENCIL_PREC_TF32X3);
+        const int k = bf ? 16 : 8;
+        const TcLines L = tc_lines_2d(shape, r, t, n, k);
+        double blocks = 0;
+        for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
+        const double products = prec == STENCIL_PREC_TF32 ? 1.0 : 3.0;
+        const double cost = std::max(kMmaCycles, 128.0 * n * k / (bf ? 4096.0 : 2048.0));
+        const double mma = blocks * products / (128.0 * n) * cost;
+        if (bf) per_out = mma + kWorkerBf16x3;
+        else per_out = std::max(mma, prec == STENCIL_PREC_TF32 ? kWorkerTf32 : kWorkerTf32x3);
+    } else {
+        return 0;
+    }
+    return t * sm_clk / per_out / 1e9;
+}
+
+// CUDA-core prediction (point updates/s / 1e9) of a plan at depth t with
+// output tile `tile`: min(P_CU / (2K) / overlap, t B / (2D)) (Eq. 8, with the
+// redundant work of overlapped temporal tiles), and for 2-D FP32 the issue
+// roof of the FP32 sub-step.
+static double cu_gstencils(const Plan &p, int t, const int tile[3])
+{
+    const stencil_peaks pk = peaks();
+    const int D = (int)p.elem_bytes();
+    const double P_cu = p.dtype == STENCIL_F64 ? pk.cu_f64_flops : pk.cu_f32_flops;
+    const int K = pattern_points(p.pat.shape, p.pat.d, p.pat.r);
+    const double ovl = cu_overlap_factor(p, t, tile);
+    double g = std::min(P_cu / (2.0 * K) / ovl, t * pk.hbm_bytes_per_s / (2.0 * D)) / 1e9;
+    if (p.dtype == STENCIL_F32 && p.pat.d == 2) {
+        const double per_out = ovl * t * K * kCuF32InstrPerTap / (128.0 * kCuF32IssueEff);
+        g = std::min(g, t * (pk.cu_f32_flops / 256.0) / per_out / 1e9);
+    }
+    return g;
+}
+
 struct Cand {
     int path, prec, t;
     double gst;
@@ -310,11 +402,7 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                     } else {
                         cu_default_tile(*p, t, c.tile);
                     }
-                    ModelOut m = model_eval(shape, d, r, t, D, 1.0, 1.0, P_cu, P_cu, B);
-                    double ovl = cu_overlap_factor(*p, t, c.tile);
-                    double comp = P_cu / (2.0 * m.K) / ovl / 1e9;
-                    double mem = t * B / (2.0 * D) / 1e9;
-                    c.gst = std::min(comp, mem);
+                    c.gst = cu_gstencils(*p, t, c.tile);
                 } else {
                     c.tile[0] = 1;
                     c.tile[1] = p->dtype == STENCIL_F64 ? 64 : 128;
@@ -328,6 +416,8 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec, slices), P_cu,
                                             tc_peak(*p, prec, path), B);
                     c.gst = m.gst_tc;
+                    const double gi = tc_instr_gstencils(*p, prec, path, t);
+                    if (gi > 0) c.gst = std::min(c.gst, gi);
                 }
                 cands.push_back(c);
             }
@@ -387,8 +477,19 @@ stencil_status dispatch(Plan *p)
     in.K = m.K;
     in.K_fused = m.K_fused;
     in.scenario = m.scenario;
-    in.predicted_cu_gstencils = m.gst_cu;
-    in.predicted_tc_gstencils = tc_supported(*p, tc_prec, tc_path) ? m.gst_tc : 0.0;
+    {
+        int cut[3];
+        if (p->path == STENCIL_PATH_CUDA_CORE) {
+            for (int i = 0; i < 3; i++) cut[i] = p->tile[i];
+        } else {
+            cu_default_tile(*p, p->t, cut);
+        }
+        in.predicted_cu_gstencils = cu_supported(shape, d, r) ? cu_gstencils(*p, p->t, cut) : 0.0;
+    }
+    double gtc = m.gst_tc;
+    const double gi = tc_instr_gstencils(*p, tc_prec, tc_path, p->t);
+    if (gi > 0) gtc = std::min(gtc, gi);
+    in.predicted_tc_gstencils = tc_supported(*p, tc_prec, tc_path) ? gtc : 0.0;
     in.predicted_gstencils = pick->gst;
     if (p->path == STENCIL_PATH_CUDA_CORE) {
         in.alpha = 1.0;

@@ -9,8 +9,11 @@ namespace {
 
 __device__ unsigned long long g_probe_sink;
 
+// Eight CTAs of 256 threads per SM for FP32 (64 warps); four for FP64, whose
+// 16 chains of doubles need 32 registers alone (eight CTAs would cap a thread
+// at 32 registers and spill the chains to local memory).
 template <typename T>
-__global__ void __launch_bounds__(256, 8) fma_chains(int iters, T seed)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 4 : 8) fma_chains(int iters, T seed)
 {
     T a[16];
 #pragma unroll
@@ -62,13 +65,13 @@ try {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "stencil_probe_peaks: device query");
     cudaStream_t st = (cudaStream_t)stream;
-    // 64 warps per SM, 16 independent chains each; about 130 ms per timed
-    // launch at the maximum clock (2 FP64 / 128 FP32 FMA lanes per SM), so the
-    // launch ramp and the clock's rise are a small part of the timed region
-    const int blocks = sms * 8;
-    stencil_status s = time_chains<double>(blocks, 1 << 14, st, &measured->cu_f64_flops);
+    // 32 (FP64) or 64 (FP32) warps per SM, 16 independent chains each; about
+    // 130 ms per timed launch at the maximum clock (2 FP64 / 128 FP32 FMA
+    // lanes per SM), so the launch ramp and the clock's rise are a small part
+    // of the timed region
+    stencil_status s = time_chains<double>(sms * 4, 1 << 15, st, &measured->cu_f64_flops);
     if (s != STENCIL_OK) return s;
-    return time_chains<float>(blocks, 1 << 20, st, &measured->cu_f32_flops);
+    return time_chains<float>(sms * 8, 1 << 20, st, &measured->cu_f32_flops);
 } catch (...) {
     return gbs::abi_exception("stencil_probe_peaks");
 }

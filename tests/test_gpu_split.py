@@ -55,7 +55,8 @@ def _interior(a, r, dims):
 
 CASES = [
     # shape, r, dims, steps, t: several 128 x 32 tiles with ragged tails,
-    # remainders, fused radii up to 8, grids smaller than a tile or the band
+    # remainders, fused radii up to 8, grids smaller than a tile or the band,
+    # and grids of more tiles than CTAs (the double-buffered pipeline)
     ("box", 3, (300, 211), 3, 1),
     ("box", 3, (131, 77), 5, 1),
     ("box", 1, (257, 300), 7, 3),
@@ -67,6 +68,9 @@ CASES = [
     ("box", 1, (5, 7), 3, 3),          # grid smaller than the band
     ("box", 3, (3, 300), 2, 1),        # three rows
     ("star", 3, (1, 1), 2, 1),         # one point
+    ("box", 3, (640, 1600), 2, 1),     # 250 tiles: persistent CTAs take a second tile
+    ("box", 1, (1024, 2048), 3, 3),    # 512 tiles, three to four per CTA
+    ("box", 2, (600, 1000), 3, 3),     # 7-digit form over 315 tiles
 ]
 
 
