@@ -772,8 +772,12 @@ def main():
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        h_in = torch.from_numpy(u).pin_memory()
-        h_out = torch.empty_like(h_in).pin_memory()
+        # host buffers from stencil_host_alloc (2 MiB pages, page-locked): with
+        # 4 KiB pinned pages the GPU's first read of the input after the
+        # previous run's seconds of HBM traffic runs at ~10 GB/s
+        h_in = B.host_empty(u.shape, cfg["dtype"])
+        h_in.copy_(torch.from_numpy(u))
+        h_out = B.host_empty(u.shape, cfg["dtype"])
 
         def copy_rates():
             # the copy rates of the pinned buffers alone (CUDA events on the stream)
@@ -804,7 +808,8 @@ def main():
         nbytes = h_in.numel() * h_in.element_size()
         e2e = {"value": whole_job_rate(world, pts, steps, args.steps, el), "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "api": "stencil_run_host (pinned host buffers)", "clocks": e2e_clocks.summary()}
+               "api": "stencil_run_host (host buffers from stencil_host_alloc: page-locked, 2 MiB pages)",
+               "clocks": e2e_clocks.summary()}
         # the copy rates of the same pinned buffers alone, before and after the
         # timed region: they split the end-to-end time into copies and compute
         e2e["h2d_gbs"], e2e["d2h_gbs"] = copy_rates()

@@ -240,6 +240,22 @@ stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_
 stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out,
                                 int64_t steps, stencil_stream_t stream);
 
+/* Page-locked host memory for stencil_run_host (a library service; no
+ * counterpart in the paper).  Allocates `bytes` (rounded up to 2 MiB) of
+ * zero-filled host memory aligned to 2 MiB, advised to use transparent huge
+ * pages and registered with CUDA (portable, so copies from it run at full
+ * speed).  GPU reads of page-locked memory mapped with 4 KiB pages drop to
+ * ~10 GB/s on Grace-based GB300 machines once their translations have gone
+ * cold (after seconds of HBM-bound kernels); with 2 MiB pages they stay near
+ * ~110 GB/s cold and ~210 GB/s warm.  The memory belongs to the caller until
+ * stencil_host_free.  INVALID_ARG for a null ptr or bytes == 0; OOM if the
+ * mapping fails; CUDA if the registration fails (nothing is left mapped). */
+stencil_status stencil_host_alloc(void **ptr, size_t bytes);
+
+/* Release memory from stencil_host_alloc (null is a no-op); INVALID_ARG for
+ * any other pointer. */
+stencil_status stencil_host_free(void *ptr);
+
 /* The zero-padded Toeplitz operands of the tensor-core path (Sec. 2.2.1-2.2.3;
  * S as in Sec. 2.2.2).
  * The tensor-core operand layout of this plan's (dtype, precision) at fusion

@@ -122,6 +122,10 @@ def load() -> ctypes.CDLL:
     L.stencil_run_noalloc.restype = st
     L.stencil_run_host.argtypes = [vp, vp, vp, i64, vp]
     L.stencil_run_host.restype = st
+    L.stencil_host_alloc.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
+    L.stencil_host_alloc.restype = st
+    L.stencil_host_free.argtypes = [vp]
+    L.stencil_host_free.restype = st
     L.stencil_plan_sptc_layout.argtypes = [vp, ctypes.c_int, ctypes.POINTER(stencil_sptc_layout), vp, vp, vp, vp, vp]
     L.stencil_plan_sptc_layout.restype = st
     L.stencil_plan_autotune.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp, ctypes.POINTER(stencil_tune_result),
@@ -354,6 +358,35 @@ def declared_symbols(header: str | None = None) -> list[str]:
 
 
 # ---- convenience wrapper over torch tensors ----------------------------------------
+
+def stencil_host_alloc(nbytes: int) -> int:
+    p = ctypes.c_void_p()
+    _check(load().stencil_host_alloc(ctypes.byref(p), int(nbytes)), "stencil_host_alloc")
+    return p.value
+
+
+def stencil_host_free(ptr: int) -> None:
+    _check(load().stencil_host_free(ptr), "stencil_host_free")
+
+
+def host_empty(shape, dtype):
+    """A CPU torch tensor of `shape` and `dtype` ("f64"/"f32") in memory from
+    stencil_host_alloc (huge-page backed, page-locked); the memory is released
+    with the tensor."""
+    import numpy as np
+    import torch
+    npdt = np.float64 if _dtype_code(dtype) == F64 else np.float32
+    count = 1
+    for n in shape:
+        count *= int(n)
+    nbytes = max(count, 1) * np.dtype(npdt).itemsize
+    ptr = stencil_host_alloc(nbytes)
+    arr = np.ctypeslib.as_array((ctypes.c_char * nbytes).from_address(ptr)).view(npdt)[:count].reshape(shape)
+    t = torch.from_numpy(arr)
+    import weakref
+    weakref.finalize(t, stencil_host_free, ptr)
+    return t
+
 
 def _resolve_device(device):
     """torch.device with the index filled in ("cuda" -> the current CUDA

@@ -251,7 +251,11 @@ static double beta_of(int precision, int slices = 0)
 constexpr double kMmaCycles = 90.0;        // per tcgen05.mma, M = 128, N <= ~176
 constexpr double kWorkerTf32 = 1.30;       // tc2d_ws TF32: in-place rounding, staging, epilogue
 constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
-constexpr double kWorkerBf16x3 = 1.18;     // tc2d_sweep BF16x3 (synchronous: added to the MMAs)
+// tc2d_sweep BF16x3 runs one tile per CTA with several CTAs per SM, whose
+// MMAs interleave: 2.65 cycles per output plus 47.6 per MMA of an output
+// (fitted to Box-2D2R at t = 1..4 within 10 %)
+constexpr double kWorkerBf16x3 = 2.65;
+constexpr double kBf16x3MmaCycles = 47.6;
 constexpr double kWorkerSplit = 4.06;      // tc2d_split: FP64 load, exponent, digit cut, recombination
 // sptc2d_sweep issues warp-level mma.sp between its staging and epilogue
 // work, so the two add: 0.92 cycles per output plus 3.15 per sparse
@@ -296,7 +300,7 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         const double products = prec == STENCIL_PREC_TF32 ? 1.0 : 3.0;
         const double cost = std::max(kMmaCycles, 128.0 * n * k / (bf ? 4096.0 : 2048.0));
         const double mma = blocks * products / (128.0 * n) * cost;
-        if (bf) per_out = mma + kWorkerBf16x3;
+        if (bf) per_out = kWorkerBf16x3 + blocks * products / (128.0 * n) * kBf16x3MmaCycles;
         else per_out = std::max(mma, prec == STENCIL_PREC_TF32 ? kWorkerTf32 : kWorkerTf32x3);
     } else {
         return 0;

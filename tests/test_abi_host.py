@@ -396,3 +396,16 @@ def test_batch_refuses_more_work_items_than_an_int_indexes(lib):
         assert B.stencil_launch_count() == n0
     finally:
         B.stencil_batch_destroy(h)
+
+
+def test_host_alloc_argument_checks_without_cuda(lib):
+    """stencil_host_alloc / stencil_host_free refuse bad arguments before any
+    CUDA call (the allocation itself needs a GPU: tests/test_gpu_host_buffer.py)."""
+    import ctypes
+    L = B.load()
+    p = ctypes.c_void_p()
+    assert L.stencil_host_alloc(None, 4096) == B.STENCIL_ERR_INVALID_ARG
+    assert L.stencil_host_alloc(ctypes.byref(p), 0) == B.STENCIL_ERR_INVALID_ARG
+    assert L.stencil_host_free(None) == B.STENCIL_OK
+    buf = ctypes.create_string_buffer(64)
+    assert L.stencil_host_free(ctypes.addressof(buf)) == B.STENCIL_ERR_INVALID_ARG
