@@ -702,13 +702,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 // ---------------------------------------------------------------------------
 // 3-D, one step per sweep (t = 1), 2.5-D streaming: a work item is a
 // (BY x BX) tile of one z chunk of CZ planes.  The CTA marches along z with a
-// ring of NP = 2R + 2 input planes (each the tile grown by R in y and x) in
-// shared memory: plane z + R + 1 is copied (cp.async) while plane z is
-// computed, so every input plane is read once per tile and the only
-// re-reads are the y/x halo.  256 threads: thread (ty, tx) = (tid / 16,
-// tid % 16) computes outputs (y, x0 .. x0 + 3) for x0 = 4 tx and the RPT rows
-// y = ty + 16 i; each (oz, oy) row segment of 4 + 2R values is loaded once
-// and used for the 4 outputs.
+// ring of NP = 2R + 1 + PF input planes (each the tile grown by R in y and x)
+// in shared memory: while plane z is computed, planes z + R + 1 ..
+// z + R + PF are in flight (cp.async, 16-byte copies where the stored rows
+// allow), so every input plane is read once per tile and the only re-reads
+// are the y/x halo.  256 threads: thread (ty, tx) = (tid / 16, tid % 16)
+// computes outputs (y, x0 .. x0 + 3) for x0 = 4 tx and the RPT rows
+// y = ty + 16 i; each (oz, oy) row segment of 4 + 2R values is read with
+// 16-byte shared loads (rows padded to 16 bytes) and used for the 4 outputs.
 // ---------------------------------------------------------------------------
 constexpr int kStreamCZ = 64;
 
@@ -718,10 +719,11 @@ __host__ __device__ constexpr int stream_rows_per_thread()
     return sizeof(T) == 4 ? 2 : 1;  // BY = 16 * RPT: 32 (FP32), 16 (FP64)
 }
 
+// Staged row pitch: BX = 64 plus the x halo, padded to 16 bytes.
 template <typename T, int R>
 __host__ __device__ constexpr int stream_pitch()
 {
-    return 64 + 2 * R;  // BX = 64 plus the x halo
+    return (64 + 2 * R + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
 }
 
 template <typename T, int R>
@@ -730,11 +732,84 @@ __host__ __device__ constexpr int stream_plane_elems()
     return (16 * stream_rows_per_thread<T>() + 2 * R) * stream_pitch<T, R>();
 }
 
+// Planes in flight ahead of the computed one: as many as fit (up to 4) in
+// ~110 KB of ring, so that two CTAs share an SM.
+template <typename T, int R>
+__host__ __device__ constexpr int stream_prefetch()
+{
+    return (110 * 1024 / (stream_plane_elems<T, R>() * (int)sizeof(T)) - (2 * R + 1)) > 4
+               ? 4
+               : ((110 * 1024 / (stream_plane_elems<T, R>() * (int)sizeof(T)) - (2 * R + 1)) < 1
+                      ? 1
+                      : (110 * 1024 / (stream_plane_elems<T, R>() * (int)sizeof(T)) - (2 * R + 1)));
+}
+
 template <typename T, int R>
 __host__ __device__ constexpr size_t stream_smem_bytes(int K)
 {
     return (sizeof(T) == 8 ? (size_t)((K * sizeof(T) + 15) / 16 * 16) : 0) +
-           (size_t)(2 * R + 2) * stream_plane_elems<T, R>() * sizeof(T);
+           (size_t)(2 * R + 1 + stream_prefetch<T, R>()) * stream_plane_elems<T, R>() * sizeof(T);
+}
+
+// Columns [lo, hi] of a thread's row segment (of 4 + 2R values) that the
+// taps of plane offset oz, row offset oy touch: x0 + R + ox + c for the ox
+// with a tap and c = 0..3 (lo > hi: no tap in this row).
+template <int SHAPE, int R>
+__host__ __device__ constexpr int seg_lo(int oz, int oy)
+{
+    int lo = 1 << 20;
+    for (int ox = -R; ox <= R; ++ox)
+        if (tap_index<SHAPE, 3, R>(oz, oy, ox) >= 0 && R + ox < lo) lo = R + ox;
+    return lo;
+}
+template <int SHAPE, int R>
+__host__ __device__ constexpr int seg_hi(int oz, int oy)
+{
+    int hi = -1;
+    for (int ox = -R; ox <= R; ++ox)
+        if (tap_index<SHAPE, 3, R>(oz, oy, ox) >= 0 && R + ox + 3 > hi) hi = R + ox + 3;
+    return hi;
+}
+
+// v[i] = rowp[i] for i in [lo, hi] with the widest shared loads their
+// alignment allows (rowp is 16-byte aligned): 16-byte, then 8-byte (FP32),
+// then single loads.  lo and hi are constants once the callers' loops over
+// the tap offsets are unrolled, so every branch folds away.
+template <typename T, int NV>
+__device__ __forceinline__ void load_seg(const T *__restrict__ rowp, T *v, int lo, int hi)
+{
+    constexpr int VE = 16 / (int)sizeof(T);
+    auto s16 = [&](int j) { return j >= 0 && j % VE == 0 && j >= lo && j + VE - 1 <= hi; };
+    auto s8 = [&](int j) {
+        return sizeof(T) == 4 && j >= 0 && j % 2 == 0 && j >= lo && j + 1 <= hi && !s16(j - j % VE);
+    };
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        if (i < lo || i > hi) continue;
+        if (s16(i)) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(rowp + i);
+                v[i] = q.x;
+                v[i + 1] = q.y;
+                v[i + 2] = q.z;
+                v[i + 3] = q.w;
+            } else {
+                const double2 q = *reinterpret_cast<const double2 *>(rowp + i);
+                v[i] = q.x;
+                v[i + 1] = q.y;
+            }
+        } else if (s16(i - i % VE)) {
+            // loaded with its 16-byte group
+        } else if (s8(i)) {
+            const float2 q = *reinterpret_cast<const float2 *>(reinterpret_cast<const float *>(rowp) + i);
+            v[i] = (T)q.x;
+            v[i + 1] = (T)q.y;
+        } else if (s8(i - i % 2)) {
+            // loaded with its 8-byte pair
+        } else {
+            v[i] = rowp[i];
+        }
+    }
 }
 
 template <typename T, int SHAPE, int R>
@@ -747,7 +822,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr bool kSmemW = sizeof(T) == 8;
     constexpr int RPT = stream_rows_per_thread<T>(), BY = 16 * RPT, BX = 64;
     constexpr int PW = stream_pitch<T, R>(), PH = BY + 2 * R, PE = stream_plane_elems<T, R>();
-    constexpr int NP = 2 * R + 2;
+    constexpr int PF = stream_prefetch<T, R>();
+    constexpr int NP = 2 * R + 1 + PF;
+    constexpr int VE = 16 / (int)sizeof(T);  // elements per 16 bytes
+    constexpr int NV = 4 + 2 * R;            // row segment of a thread
+    constexpr int NL = (NV + VE - 1) / VE;   // 16-byte loads per row segment
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *wsm = reinterpret_cast<T *>(smem_raw);
     if (kSmemW) {
@@ -757,6 +836,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ty = tid >> 4, tx = tid & 15, x0 = 4 * tx;
     const int64_t nz = Ez - 2 * R, ny = Ey - 2 * R, nx = Ex - 2 * R;
+    // rows start on 16-byte boundaries in global memory when the stored row
+    // length is a 16-byte multiple and `in` is aligned (the staged window of
+    // every tile starts at column 64 bx, a 16-byte multiple)
+    const bool vec = (Ex * (int64_t)sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
 
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int bx = item % tiles_x, by = (item / tiles_x) % tiles_y, bz = item / (tiles_x * tiles_y);
@@ -765,6 +848,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int64_t rem = nz - (Z0 - R);
         const int nzo = (int)(rem < kStreamCZ ? rem : kStreamCZ);  // output planes of this item
         const int64_t zfirst = Z0 - R;                                // first input plane
+        const int nin = nzo + 2 * R;                                  // input planes of the item
         // copy input plane gz (rows Y0-R.., columns X0-R.., zero outside the
         // stored grid) into its ring slot
         auto load_plane = [&](int64_t gz) {
@@ -774,21 +858,32 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const int64_t gy = Y0 - R + row;
                 const bool rok = zok && gy >= 0 && gy < Ey;
                 const T *src = in + ((rok ? gz : 0) * Ey + (rok ? gy : 0)) * Ex;
-                for (int c = lane; c < PW; c += 32) {
+                for (int c = lane * VE; c < PW; c += 32 * VE) {
                     const int64_t gx = X0 - R + c;
-                    const bool ok = rok && gx >= 0 && gx < Ex;
-                    cp_async_elem<sizeof(T)>(dst + row * PW + c, ok ? src + gx : in, ok);
+                    if (vec && rok && gx + VE <= Ex) {
+                        cp_async_elem<16>(dst + row * PW + c, src + gx, true);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < VE; ++e) {
+                            const bool ok = rok && gx + e < Ex;
+                            cp_async_elem<sizeof(T)>(dst + row * PW + c + e, ok ? src + gx + e : in, ok);
+                        }
+                    }
                 }
             }
         };
         __syncthreads();  // the previous item's reads of the ring are done
+        // planes 0 .. 2R (the first output's) and the PF planes after them
         for (int k = 0; k < 2 * R + 1; ++k) load_plane(zfirst + k);
         cp_async_commit();
-        for (int zo = 0; zo < nzo; ++zo) {
-            // planes zo .. zo + 2R (relative to zfirst) are needed; prefetch the next
-            if (zo + 1 < nzo) load_plane(zfirst + zo + 2 * R + 1);
+#pragma unroll
+        for (int f = 0; f < PF; ++f) {
+            if (2 * R + 1 + f < nin) load_plane(zfirst + 2 * R + 1 + f);
             cp_async_commit();
-            cp_async_wait_group<1>();  // everything but the newest plane has landed
+        }
+        for (int zo = 0; zo < nzo; ++zo) {
+            // planes zo .. zo + 2R are needed: all but the PF newest groups
+            cp_async_wait_group<PF>();
             __syncthreads();
             T acc[RPT][4];
 #pragma unroll
@@ -805,9 +900,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                     for (int i = 0; i < RPT; ++i) {
                         const T *rowp = pl + (ty + 16 * i + R + oy) * PW + x0;
-                        T v[4 + 2 * R];
-#pragma unroll
-                        for (int c = 0; c < 4 + 2 * R; ++c) v[c] = rowp[c];
+                        T v[NL * VE];
+                        load_seg<T, NL * VE>(rowp, v, seg_lo<SHAPE, R>(oz, oy), seg_hi<SHAPE, R>(oz, oy));
 #pragma unroll
                         for (int ox = -R; ox <= R; ++ox) {
                             const int k = tap_index<SHAPE, 3, R>(oz, oy, ox);
@@ -832,7 +926,9 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (gx - R < nx) orow[gx] = acc[i][c];
                 }
             }
-            __syncthreads();  // plane zo is no longer read before its slot is refilled
+            __syncthreads();  // plane zo is no longer read: its slot takes plane zo + 2R + 1 + PF
+            if (zo + 2 * R + 1 + PF < nin) load_plane(zfirst + zo + 2 * R + 1 + PF);
+            cp_async_commit();
         }
     }
     cp_async_wait_group<0>();
