@@ -88,14 +88,21 @@ typedef enum {
  * significant bits), the S(S+1)/2 digit products of each level run on the
  * FP16 tensor cores with exact FP32 sums, and the levels are recombined in
  * 64-bit integers: FP64 accuracy (a few units of 2^-53 per sweep,
- * normwise).  ANY: the dispatcher may pick any form the grid type allows. */
+ * normwise).  F16 / F16X3 (FP32 grids, tensor-core path): FP16 operands with
+ * a power-of-two scale per staged tile (and one for the composite weights),
+ * one product (F16: 11 significant bits, TF32's) or hi + lo parts with three
+ * products (F16X3: 22 bits, TF32x3's), FP32 accumulation; a kind::f16 MMA
+ * takes K = 16 per instruction against TF32's 8.  ANY: the dispatcher may
+ * pick any form the grid type allows. */
 typedef enum {
     STENCIL_PREC_NATIVE = 0,
     STENCIL_PREC_TF32 = 1,
     STENCIL_PREC_TF32X3 = 2,
     STENCIL_PREC_BF16X3 = 3,
     STENCIL_PREC_ANY = 4,
-    STENCIL_PREC_OZAKI = 5
+    STENCIL_PREC_OZAKI = 5,
+    STENCIL_PREC_F16 = 6,
+    STENCIL_PREC_F16X3 = 7
 } stencil_precision;
 
 /* Peak rates the model uses (bytes/s and FLOP/s).  Table 1 of the paper:
@@ -189,8 +196,9 @@ stencil_status stencil_plan_create(stencil_plan **plan, stencil_shape shape, int
  * 3.2.3 tensor cores, Sec. 4.3 sparse tensor cores; the split-precision forms
  * have no counterpart in the paper).  Keys and values:
  *   "path"      auto | cuda_core | tensor_core | sparse_tensor_core
- *   "precision" native | tf32 | tf32x3 | bf16x3 | ozaki | any   (FP32 grids:
- *               native, tf32, tf32x3, bf16x3, any; FP64 grids: native, ozaki,
+ *   "precision" native | tf32 | tf32x3 | bf16x3 | f16 | f16x3 | ozaki | any
+ *               (FP32 grids: native, tf32, tf32x3, bf16x3, f16, f16x3, any;
+ *               FP64 grids: native, ozaki,
  *               any.  ozaki runs on the tensor-core path only, 2-D, fused
  *               radius t*r <= 8 with 9-bit digits, <= 6 with 8-bit digits)
  *   "t"         0 (model) or 1..16

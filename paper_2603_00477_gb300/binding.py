@@ -21,9 +21,9 @@ STENCIL_OK, STENCIL_ERR_INVALID_ARG, STENCIL_ERR_UNSUPPORTED, STENCIL_ERR_CUDA, 
 BOX, STAR = 0, 1
 F64, F32 = 0, 1
 PATH_AUTO, PATH_CUDA_CORE, PATH_TENSOR_CORE, PATH_SPARSE_TENSOR_CORE = range(4)
-PREC_NATIVE, PREC_TF32, PREC_TF32X3, PREC_BF16X3, PREC_ANY, PREC_OZAKI = range(6)
+PREC_NATIVE, PREC_TF32, PREC_TF32X3, PREC_BF16X3, PREC_ANY, PREC_OZAKI, PREC_F16, PREC_F16X3 = range(8)
 PATH_NAMES = {0: "auto", 1: "cuda_core", 2: "tensor_core", 3: "sparse_tensor_core"}
-PREC_NAMES = {0: "native", 1: "tf32", 2: "tf32x3", 3: "bf16x3", 4: "any", 5: "ozaki"}
+PREC_NAMES = {0: "native", 1: "tf32", 2: "tf32x3", 3: "bf16x3", 4: "any", 5: "ozaki", 6: "f16", 7: "f16x3"}
 
 
 class StencilError(RuntimeError):

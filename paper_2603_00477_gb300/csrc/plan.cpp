@@ -164,10 +164,13 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
         g.n_tile = 16;  // tcgen05 kind::f16: 16 output columns per digit block, K = 16
         g.k_inst = 16;
     } else if (dtype == STENCIL_F64) g.k_inst = 4;             // FP64 MMA m8n8k4
-    else if (precision == STENCIL_PREC_BF16X3) g.k_inst = 16;  // kind::f16 K = 16
+    else if (precision == STENCIL_PREC_BF16X3 || precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3)
+        g.k_inst = 16;                                         // kind::f16 K = 16
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
         g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
+    if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3))
+        g.n_tile = std::max(16, tc_wsh_ntile(shape, r, t, precision == STENCIL_PREC_F16X3));
     if (d == 2 && path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
         // mma.sp m16n8k16: 16 output columns per block, logical K 16
         SpLayout L = sp_layout_2d(shape, r, t);
@@ -211,7 +214,8 @@ bool tc_supported(const Plan &p, int precision, int path)
         return p.dtype == STENCIL_F32 && precision == STENCIL_PREC_TF32;
     if (path != STENCIL_PATH_TENSOR_CORE) return false;
     if (p.dtype == STENCIL_F64) return precision == STENCIL_PREC_NATIVE || precision == STENCIL_PREC_OZAKI;
-    return precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3;
+    return precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3 ||
+           precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3;
 }
 
 static double tc_peak(const Plan &p, int precision, int path)
@@ -220,7 +224,8 @@ static double tc_peak(const Plan &p, int precision, int path)
     const bool sparse = path == STENCIL_PATH_SPARSE_TENSOR_CORE;
     if (p.dtype == STENCIL_F64 && precision == STENCIL_PREC_OZAKI) return pk.tc_bf16_flops;  // FP16 = BF16 rate
     if (p.dtype == STENCIL_F64) return pk.tc_f64_flops;
-    if (precision == STENCIL_PREC_BF16X3) return sparse ? pk.sptc_bf16_flops : pk.tc_bf16_flops;
+    if (precision == STENCIL_PREC_BF16X3 || precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3)
+        return sparse ? pk.sptc_bf16_flops : pk.tc_bf16_flops;  // FP16 and BF16 share the dense rate
     return sparse ? pk.sptc_tf32_flops : pk.tc_tf32_flops;
 }
 
@@ -229,7 +234,9 @@ static double tc_peak(const Plan &p, int precision, int path)
 static double beta_of(int precision, int slices = 0)
 {
     if (precision == STENCIL_PREC_OZAKI) return slices * (slices + 1) / 2.0;
-    return (precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3) ? 3.0 : 1.0;
+    return (precision == STENCIL_PREC_TF32X3 || precision == STENCIL_PREC_BF16X3 || precision == STENCIL_PREC_F16X3)
+               ? 3.0
+               : 1.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -251,6 +258,8 @@ static double beta_of(int precision, int slices = 0)
 constexpr double kMmaCycles = 90.0;        // per tcgen05.mma, M = 128, N <= ~176
 constexpr double kWorkerTf32 = 1.30;       // tc2d_ws TF32: in-place rounding, staging, epilogue
 constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
+constexpr double kWorkerF16 = 1.60;        // tc2d_wsh F16: staging, exponent, conversion, epilogue
+constexpr double kWorkerF16x3 = 2.00;      // tc2d_wsh F16x3: + the lo parts
 // tc2d_sweep BF16x3 runs one tile per CTA with several CTAs per SM, whose
 // MMAs interleave: 2.65 cycles per output plus 47.6 per MMA of an output
 // (fitted to Box-2D2R at t = 1..4 within 10 %)
@@ -290,6 +299,15 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
         const double mma = blocks * S / (128.0 * 16.0) * kMmaCycles;
         per_out = std::max(mma, kWorkerSplit);
+    } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3)) {
+        const int n = tc_wsh_ntile(shape, r, t, prec == STENCIL_PREC_F16X3);
+        if (n == 0) return 0;
+        const TcLines L = tc_lines_2d(shape, r, t, n, 16);
+        double blocks = 0;
+        for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
+        const double products = prec == STENCIL_PREC_F16 ? 1.0 : 3.0;
+        const double mma = blocks * products / (128.0 * n) * std::max(kMmaCycles, 128.0 * n * 16 / 4096.0);
+        per_out = std::max(mma, prec == STENCIL_PREC_F16 ? kWorkerF16 : kWorkerF16x3);
     } else if (p.dtype == STENCIL_F32) {
         const bool bf = prec == STENCIL_PREC_BF16X3;
         const int n = bf ? 8 : tc_ws_ntile(shape, r, t, prec == STENCIL_PREC_TF32X3);
@@ -366,6 +384,8 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
             precs.push_back(STENCIL_PREC_TF32);
             precs.push_back(STENCIL_PREC_TF32X3);
             precs.push_back(STENCIL_PREC_BF16X3);
+            precs.push_back(STENCIL_PREC_F16);
+            precs.push_back(STENCIL_PREC_F16X3);
         } else {
             precs.push_back(STENCIL_PREC_OZAKI);
         }
@@ -415,6 +435,12 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                     if (prec == STENCIL_PREC_OZAKI) {
                         c.tile[1] = 128;
                         c.tile[2] = 16 * split_nacc(t * r, slices);
+                    }
+                    if (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
+                        const int tn = tc_wsh_ntile(shape, r, t, prec == STENCIL_PREC_F16X3);
+                        if (tn == 0) continue;  // the tile does not fit
+                        c.tile[1] = 128;
+                        c.tile[2] = 2 * tn;
                     }
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec, slices), P_cu,
@@ -596,8 +622,10 @@ try {
         else if (v == "tf32x3") trial.req_precision = STENCIL_PREC_TF32X3;
         else if (v == "bf16x3") trial.req_precision = STENCIL_PREC_BF16X3;
         else if (v == "ozaki") trial.req_precision = STENCIL_PREC_OZAKI;
+        else if (v == "f16") trial.req_precision = STENCIL_PREC_F16;
+        else if (v == "f16x3") trial.req_precision = STENCIL_PREC_F16X3;
         else if (v == "any") trial.req_precision = STENCIL_PREC_ANY;
-        else return fail(STENCIL_ERR_INVALID_ARG, "precision must be native|tf32|tf32x3|bf16x3|ozaki|any");
+        else return fail(STENCIL_ERR_INVALID_ARG, "precision must be native|tf32|tf32x3|bf16x3|f16|f16x3|ozaki|any");
         if (trial.dtype == STENCIL_F64 && trial.req_precision != STENCIL_PREC_NATIVE &&
             trial.req_precision != STENCIL_PREC_ANY && trial.req_precision != STENCIL_PREC_OZAKI)
             return fail(STENCIL_ERR_INVALID_ARG, "FP64 grids take precision native, ozaki or any");

@@ -85,6 +85,30 @@ inline int tc_ws_ntile(int shape, int r, int t, bool split)
     return 8;
 }
 
+// Shared memory of the FP16 warp-specialised kernel (tc2d_wsh) at MMA N = n,
+// nacc column blocks per tile, nkb K blocks of 16 per line: a 256-byte
+// header, the FP16 Toeplitz blocks (x2 split), two FP32 staging buffers and
+// two FP16 operand buffers (x2 split) of 128 + 2R rows (odd) by the window of
+// (nacc - 1) n + 16 nkb columns.
+inline size_t tc_wsh_smem(int R, int nkb, int n, int nacc, bool split)
+{
+    const size_t hs = (size_t)((128 + 2 * R) | 1);
+    const size_t nch = (size_t)(n * (nacc - 1) + 16 * nkb) / 8;
+    const size_t raw = 2 * nch * hs * 16, a = nch * hs * 16;
+    const size_t b = (size_t)(2 * R + 1) * nkb * (n / 8) * 256;
+    return 256 + b * (split ? 2 : 1) + 2 * raw + a * (split ? 4 : 2);
+}
+
+// MMA N of the FP16 kernel: 32 if its tiles fit in 227 KB, else 16, else 0.
+inline int tc_wsh_ntile(int shape, int r, int t, bool split)
+{
+    for (int n : {32, 16}) {
+        TcLines L = tc_lines_2d(shape, r, t, n, 16);
+        if (tc_wsh_smem(t * r, L.nkb, n, 2, split) <= 227 * 1024) return n;
+    }
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // 2:4-structured sparse form (paper Sec. 4.3), TF32 1:2 on mma.sp m16n8k16.
 //

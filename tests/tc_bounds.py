@@ -26,7 +26,11 @@ ceil((16 + 2R)/4); that independent count is the sparse n_mma.
 """
 from paper_2603_00477_gb300 import binding as B
 
-P_FORM = {"tf32": 2.0 * 2 ** -11, "tf32x3": 2.0 ** -21, "bf16x3": 2.0 ** -15}
+# F16 / F16X3 (FP16 operands scaled by a power of two per tile and for the
+# weights) keep 11 significant bits relative to the tile's largest value, like
+# TF32 (normwise), and hi + lo 22 bits, like TF32x3
+P_FORM = {"tf32": 2.0 * 2 ** -11, "tf32x3": 2.0 ** -21, "bf16x3": 2.0 ** -15,
+          "f16": 2.0 * 2 ** -11, "f16x3": 2.0 ** -21}
 
 
 def line_half(shape: str, r: int, t: int, a: int) -> int:
@@ -74,7 +78,7 @@ def mma_per_output(plan_handle, shape: str, r: int, t: int, split: bool) -> int:
 
 
 def tc_bound(form: str, steps: int, t: int, plan_handle, shape: str, r: int) -> float:
-    n_mma = mma_per_output(plan_handle, shape, r, t, form != "tf32")
+    n_mma = mma_per_output(plan_handle, shape, r, t, form not in ("tf32", "f16"))
     return sweeps(steps, t) * (P_FORM[form] + n_mma * 2.0 ** -23)
 
 

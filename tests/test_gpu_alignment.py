@@ -57,6 +57,8 @@ CASES = [
     ("tensor_core", "tf32", "box", 2, (140, 316), 4, 2),      # 320
     ("tensor_core", "tf32", "box", 2, (133, 252), 3, 3),      # 256, R = 6: shifted grid
     ("tensor_core", "tf32x3", "star", 1, (129, 198), 4, 1),   # 200, R = 1: shifted grid
+    ("tensor_core", "f16", "box", 2, (140, 316), 4, 2),       # 320
+    ("tensor_core", "f16x3", "box", 2, (133, 252), 3, 3),     # 256, R = 6
     ("sparse_tensor_core", "tf32", "box", 2, (200, 316), 3, 3),
     ("sparse_tensor_core", "tf32", "star", 3, (130, 250), 4, 2),
     ("sparse_tensor_core", "tf32", "box", 1, (77, 126), 3, 3),

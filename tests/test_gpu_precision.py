@@ -34,7 +34,8 @@ def problem():
     return w, u, refs
 
 
-FORMS = [("cuda_core", "native", 2)] + [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3") for t in (1, 2, 4)]
+FORMS = [("cuda_core", "native", 2)] + [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3", "f16", "f16x3")
+                                         for t in (1, 2, 4)]
 
 
 @pytest.mark.parametrize("path,prec,t", FORMS)

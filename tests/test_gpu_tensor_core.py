@@ -21,7 +21,7 @@ from tc_bounds import tc_bound
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"native64": 1e-12, "tf32x3": 1e-5, "bf16x3": 5e-5, "tf32": 3e-3}
+TOL = {"native64": 1e-12, "tf32x3": 1e-5, "bf16x3": 5e-5, "tf32": 3e-3, "f16": 3e-3, "f16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -68,6 +68,14 @@ CASES = [
     ("box", 3, (131, 77), 8, 4, "f64", "native"),
     ("star", 2, (70, 200), 6, 3, "f64", "native"),
     ("box", 1, (3, 300), 4, 2, "f64", "native"),
+    ("box", 2, (257, 300), 4, 2, "f32", "f16"),
+    ("box", 2, (200, 131), 8, 4, "f32", "f16"),        # R = 8
+    ("star", 2, (190, 260), 6, 3, "f32", "f16"),
+    ("box", 1, (130, 140), 1, 1, "f32", "f16x3"),
+    ("box", 2, (300, 500), 5, 2, "f32", "f16x3"),      # remainder sweep t' = 1; more tiles than SMs
+    ("box", 3, (140, 75), 5, 2, "f32", "f16x3"),       # R = 6: N = 16
+    ("star", 1, (128, 128), 7, 4, "f32", "f16x3"),
+    ("box", 1, (5, 7), 3, 3, "f32", "f16"),            # grid smaller than the band
 ]
 
 
@@ -88,7 +96,8 @@ def test_tc_matches_oracle(torch, shape, r, dims, steps, t, dtype, prec):
     assert not np.isnan(y).any()
 
 
-@pytest.mark.parametrize("dtype,prec", [("f64", "native"), ("f32", "tf32"), ("f32", "tf32x3"), ("f32", "bf16x3")])
+@pytest.mark.parametrize("dtype,prec", [("f64", "native"), ("f32", "tf32"), ("f32", "tf32x3"), ("f32", "bf16x3"),
+                                        ("f32", "f16"), ("f32", "f16x3")])
 @pytest.mark.parametrize("shape,r", [("box", 3), ("star", 2), ("box", 1)])
 def test_tc_dyadic_one_step_bitwise(torch, dtype, prec, shape, r):
     """Weights k/64 (k <= 8) and integer fields below 2^8 are exact in TF32 and
@@ -137,7 +146,7 @@ def test_config_box2d3r_16384_fp64_mma_sampled(torch, t):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("prec,t", [("tf32", 4), ("tf32x3", 2), ("bf16x3", 3)])
+@pytest.mark.parametrize("prec,t", [("tf32", 4), ("tf32x3", 2), ("bf16x3", 3), ("f16", 4), ("f16x3", 2)])
 def test_config_box2d2r_16384_f32_sampled(torch, prec, t):
     """Box-2D2R FP32 on 16384^2 (smooth sine-mode field), 40 steps, sampled."""
     dims = (16384, 16384)
