@@ -377,14 +377,15 @@ def fusion_leg(B, inputs, stream, dims=(4096, 4096), tmax=8):
     return {"workload": f"FP64 {'x'.join(map(str, dims))}, one fused sweep of depth t per row", "rows": rows}
 
 
-def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
+def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100, fine=10):
     """Box-2D2R FP32 16384^2 (sine-mode field): plain FP32 on CUDA cores
-    against the tensor-core TF32, TF32x3 and BF16x3 forms and the sparse TF32
-    form at each t = 1..4 (point-updates/s over `steps`-step runs), then, for
-    plain FP32 and each form at its fastest t, the normwise relative error
-    every `every` steps up to `horizon` steps against the FP64 CUDA-core path
-    run on the GPU from the same field (the reference the GPU tests hold
-    within 1e-12 of the FP64 oracle)."""
+    against the tensor-core TF32, TF32x3, BF16x3, F16 and F16x3 forms and the
+    sparse TF32 form at each t = 1..4 (point-updates/s over `steps`-step
+    runs), then, for plain FP32 and each form at its fastest t, the normwise
+    relative error every `fine` steps up to `every` steps and every `every`
+    steps up to `horizon` steps against the FP64 CUDA-core path run on the GPU
+    from the same field (the reference the GPU tests hold within 1e-12 of the
+    FP64 oracle)."""
     import numpy as np
     import torch
     dims = (16384, 16384)
@@ -394,7 +395,7 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
     pts = dims[0] * dims[1]
     rows = []
     cands = [("cuda_core", "native", t) for t in (1, 2, 3, 4)] + \
-            [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3") for t in (1, 2, 3, 4)] + \
+            [("tensor_core", p, t) for p in ("tf32", "tf32x3", "bf16x3", "f16", "f16x3") for t in (1, 2, 3, 4)] + \
             [("sparse_tensor_core", "tf32", t) for t in (1, 2, 3, 4)]
     for path, prec, t in cands:
         plan = B.Plan("box", 2, 2, w, "f32", dims, t)
@@ -420,15 +421,19 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
                           "cuda_core_gstencils": next(r["gstencils"] for r in at if r["path"] == "cuda_core"),
                           "best_tensor_gstencils": max(r["gstencils"] for r in at if r["path"] != "cuda_core")})
 
-    # error growth: FP64 reference states every `every` steps (kept on the GPU)
+    # error growth: FP64 reference states every `fine` steps to `every`, then
+    # every `every` steps (kept on the GPU)
+    marks = list(range(fine, every, fine)) + list(range(every, horizon + 1, every))
     ref_plan = B.Plan("box", 2, 2, w, "f64", dims, 0)
     ref_plan.set_option("path", "cuda_core")
     a64 = x.double()
     b64 = torch.empty_like(a64)
     ref_plan.ensure_workspace(a64.device)
     refs = []
-    for _ in range(horizon // every):
-        ref_plan.run(a64, b64, every)
+    done_steps = 0
+    for m in marks:
+        ref_plan.run(a64, b64, m - done_steps)
+        done_steps = m
         refs.append(b64[2:-2, 2:-2].clone())
         a64, b64 = b64, a64
     ref_plan.close()
@@ -447,37 +452,43 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100):
         plan.ensure_workspace(x.device)
         a, b = x.clone(), torch.empty_like(x)
         curve = []
-        for k, ref in enumerate(refs):
-            plan.run(a, b, every)
+        done_steps = 0
+        for m, ref in zip(marks, refs):
+            plan.run(a, b, m - done_steps)  # runs restart the fused schedule at each mark
+            done_steps = m
             d = (b[2:-2, 2:-2].double() - ref).abs().max() / ref.abs().max()
-            curve.append({"steps": (k + 1) * every, "rel_linf": float(d)})
+            curve.append({"steps": m, "rel_linf": float(d)})
             a, b = b, a
         plan.close()
         del a, b
+        held = 0
+        for c in curve:
+            if c["rel_linf"] > 2e-6:
+                break
+            held = c["steps"]
         errors.append({"path": path, "precision": prec, "t": r["t"], "gstencils": r["gstencils"],
-                       "error_vs_fp64": curve,
-                       "meets_2e-6_at": [c["steps"] for c in curve if c["rel_linf"] <= 2e-6]})
+                       "error_vs_fp64": curve, "within_2e-6_up_to_steps": held})
     del refs, x, y
     torch.cuda.empty_cache()
     return {"workload": f"Box-2D2R F32 16384x16384, sine-mode field, {steps} steps per timed run; "
                         f"error every {every} steps to {horizon}",
-            "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests)",
+            "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests, "
+                               "16384^2 x 100 steps on sampled boxes included)",
             "plain_fp32_cuda_core_gstencils": plain, "best": best, "crossover": crossover, "rows": rows,
             "errors": errors}
 
 
-def split_fp64_leg(B, cfg, w, u, x, y_plain, plain_gstencils, stream, reps):
+def split_fp64_leg(B, cfg, w, x, y_plain, plain_gstencils, stream, reps):
     """FP64 on the FP16 tensor cores by exact splitting (precision "ozaki")
     on the headline FP64 workload, next to the plain FP64 path already timed:
     point-updates/s over `reps` runs (CUDA events), the normwise error against
-    the plain path's result on the whole grid and against the CPU oracle on
-    two sampled boxes, and the tensor-core work of its kernel (tc2d_split):
+    the plain path's result on the whole grid (the GPU tests hold both paths
+    within 1e-12 of the oracle, on this grid and step count on sampled boxes),
+    and the tensor-core work of its kernel (tc2d_split):
     useful FP64 FLOP (2K per point-step) and issued FP16 MMA FLOP (the model's
     beta/S times the useful work, beta = S(S+1)/2 digit products)."""
-    import numpy as np
     import torch
 
-    import oracle
     dims, steps = cfg["dims"], cfg["steps"]
     if cfg["d"] != 2:
         return None
@@ -497,12 +508,6 @@ def split_fp64_leg(B, cfg, w, u, x, y_plain, plain_gstencils, stream, reps):
     r = cfg["r"]
     inner = (slice(r, -r), slice(r, -r))
     err_plain = float((z[inner] - y_plain[inner]).abs().max() / y_plain[inner].abs().max())
-    samples = [((0, 0), (4, 4)), ((dims[0] // 2, dims[1] // 2), (dims[0] // 2 + 3, dims[1] // 2 + 5))]
-    got, ref = [], []
-    for lo, hi in samples:
-        ref.append(oracle.run_region(cfg["shape"], 2, r, w, dims, u, steps, lo, hi).ravel())
-        got.append(z[lo[0] + r:hi[0] + r, lo[1] + r:hi[1] + r].cpu().numpy().ravel())
-    err_oracle = oracle.rel_linf(np.concatenate(got), np.concatenate(ref))
     t = info["t"]
     nsweeps = steps // t + (1 if steps % t else 0)
     launch_s = sec / nsweeps
@@ -518,8 +523,7 @@ def split_fp64_leg(B, cfg, w, u, x, y_plain, plain_gstencils, stream, reps):
             "t": t, "digit_slices": S, "products_per_useful_product": info["beta"], "sparsity": info["sparsity"],
             "gstencils": value, "vs_plain_fp64": value / plain_gstencils if plain_gstencils else None,
             "model_gstencils": info["predicted_gstencils"],
-            "rel_linf_vs_plain_fp64_gpu": err_plain, "rel_linf_vs_oracle_sampled": err_oracle,
-            "oracle_samples": [[list(lo), list(hi)] for lo, hi in samples],
+            "rel_linf_vs_plain_fp64_gpu": err_plain,
             "kernel": {"name": "tc2d_split", "avg_launch_ms": launch_s * 1e3,
                        "useful_fp64_tflops": useful / launch_s / 1e12,
                        "issued_fp16_tflops": issued / launch_s / 1e12, "peak_tflops": peak,
@@ -825,7 +829,7 @@ def main():
             info["precision_name"] != "ozaki":
         import oracle
         oracle.build()
-        split_leg = split_fp64_leg(B, cfg, w, u, x, y, value / world, stream, args.steps)
+        split_leg = split_fp64_leg(B, cfg, w, x, y, value / world, stream, args.steps)
 
     # per-(path, t) sweep of the headline workload next to the model's prediction
     sweep = None

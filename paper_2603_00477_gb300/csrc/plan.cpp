@@ -258,8 +258,9 @@ static double beta_of(int precision, int slices = 0)
 constexpr double kMmaCycles = 90.0;        // per tcgen05.mma, M = 128, N <= ~176
 constexpr double kWorkerTf32 = 1.30;       // tc2d_ws TF32: in-place rounding, staging, epilogue
 constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
-constexpr double kWorkerF16 = 1.60;        // tc2d_wsh F16: staging, exponent, conversion, epilogue
-constexpr double kWorkerF16x3 = 2.00;      // tc2d_wsh F16x3: + the lo parts
+constexpr double kWorkerF16 = 2.20;        // tc2d_wsh F16: staging, exponent, conversion, epilogue
+constexpr double kWorkerF16x3 = 2.40;      // tc2d_wsh F16x3: + the lo parts
+constexpr double kMmaCyclesWsh = 110.0;    // tc2d_wsh: its MMAs share shared memory with the conversion
 // tc2d_sweep BF16x3 runs one tile per CTA with several CTAs per SM, whose
 // MMAs interleave: 2.65 cycles per output plus 47.6 per MMA of an output
 // (fitted to Box-2D2R at t = 1..4 within 10 %)
@@ -306,7 +307,7 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         double blocks = 0;
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
         const double products = prec == STENCIL_PREC_F16 ? 1.0 : 3.0;
-        const double mma = blocks * products / (128.0 * n) * std::max(kMmaCycles, 128.0 * n * 16 / 4096.0);
+        const double mma = blocks * products / (128.0 * n) * std::max(kMmaCyclesWsh, 128.0 * n * 16 / 4096.0);
         per_out = std::max(mma, prec == STENCIL_PREC_F16 ? kWorkerF16 : kWorkerF16x3);
     } else if (p.dtype == STENCIL_F32) {
         const bool bf = prec == STENCIL_PREC_BF16X3;
