@@ -827,8 +827,6 @@ def main():
     split_leg = None
     if not args.no_extras and rank == 0 and cfg["dtype"] == "f64" and cfg["d"] == 2 and \
             info["precision_name"] != "ozaki":
-        import oracle
-        oracle.build()
         split_leg = split_fp64_leg(B, cfg, w, x, y, value / world, stream, args.steps)
 
     # per-(path, t) sweep of the headline workload next to the model's prediction

@@ -390,6 +390,114 @@ __device__ __forceinline__ void f32_substep4(const float *__restrict__ src, floa
     }
 }
 
+// FP32 sub-step, fixed-strip form: the fast case of f32_substep4 (every point
+// of the region interior, no band, whole quads: cw a multiple of 4,
+// ch >= S).  A work item is a quad of columns and S output rows, S a
+// compile-time constant: the S + 2R input rows are unrolled completely, so
+// each input row goes exactly into the outputs it touches (no partial sums
+// of rows outside the strip, no slot rotation) and every index is a
+// constant.  When ch is not a multiple of S the last strip of a column
+// starts at hiY - S and overlaps the one above; the overlapping outputs are
+// computed twice with identical values.  Stores are 16- or 8-byte vectors
+// (the alignment of x0 + x is the same for every item of the sub-step).
+template <int SHAPE, int R, int D, int S, typename WT>
+__device__ __forceinline__ void f32_substep4_fixed(const float *__restrict__ src, float *__restrict__ dst,
+                                                   float *__restrict__ out, const WT &wt, int P, int lo, int hiY,
+                                                   int hiX, int64_t Y0, int64_t X0, int64_t Ex, bool last)
+{
+    constexpr int NV = 2 * R + 4 + D;  // window values per row
+    constexpr int NL = (NV + 3) / 4;   // 16-byte loads per row
+    constexpr int NR = S + 2 * R;      // input rows per strip
+    const int nquads = (hiX - lo) >> 2;
+    const int nstrips = (hiY - lo + S - 1) / S;
+    const int nitems = nquads * nstrips;
+    // outputs: (row y, column x) of the region is obase[off0 + y * pitch + x]
+    float *const obase = last ? out : dst;
+    const int64_t off0 = last ? Y0 * Ex + X0 : 0;
+    const int64_t pitch = last ? Ex : P;
+    // element offset of the first output within its 16-byte chunk: the same
+    // for every item when the pitch is a multiple of 4 (else scalar stores)
+    const int phase = (pitch & 3) ? 1
+                                  : (int)(((reinterpret_cast<uintptr_t>(obase) >> 2) +
+                                           (uint64_t)(off0 + (int64_t)lo * pitch + lo)) & 3);
+    for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
+        const int sy = item / nquads, qx = item - sy * nquads;
+        const int y0 = min(lo + sy * S, hiY - S);
+        const int x = lo + 4 * qx;
+        const float4 *rp = reinterpret_cast<const float4 *>(src + (y0 - R) * P + x - R - D);
+        const int p4 = P >> 2;
+        float acc[S][4];
+#pragma unroll
+        for (int j = 0; j < S; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            float v[4 * NL];
+#pragma unroll
+            for (int c = 0; c < NL; ++c) {
+                const float4 t4 = rp[q * p4 + c];
+                v[4 * c] = t4.x;
+                v[4 * c + 1] = t4.y;
+                v[4 * c + 2] = t4.z;
+                v[4 * c + 3] = t4.w;
+            }
+            // input row q (row y0 - R + q) feeds outputs j = q - R - oy, oy in [-R, R]
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const int oy = q - R - j;
+                if (oy < -R || oy > R) continue;
+#pragma unroll
+                for (int ox = -R; ox <= R; ++ox) {
+                    const int k = tap_index<SHAPE, 2, R>(0, oy, ox);
+                    if (k >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[j][c] = fmaf(wt.w[k], v[D + R + ox + c], acc[j][c]);
+                    }
+                }
+            }
+        }
+        float *o = obase + (off0 + (int64_t)y0 * pitch + x);
+        if (phase == 0) {
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+                *reinterpret_cast<float4 *>(o + j * pitch) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+        } else if (phase == 2) {
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                float2 *o2 = reinterpret_cast<float2 *>(o + j * pitch);
+                o2[0] = make_float2(acc[j][0], acc[j][1]);
+                o2[1] = make_float2(acc[j][2], acc[j][3]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o[j * pitch + c] = acc[j][c];
+        }
+    }
+}
+
+// Selects the window phase D = (lo - R) mod 4 and the strip height (4 or 8)
+// of f32_substep4_fixed.
+template <int SHAPE, int R, typename WT>
+__device__ __forceinline__ void f32_fixed_dispatch(int D, bool s4, const float *__restrict__ src,
+                                                   float *__restrict__ dst, float *__restrict__ out, const WT &wt,
+                                                   int P, int lo, int hiY, int hiX, int64_t Y0, int64_t X0,
+                                                   int64_t Ex, bool last)
+{
+#define GBS_FIXED(DD)                                                                                          \
+    if (s4)                                                                                                    \
+        f32_substep4_fixed<SHAPE, R, DD, 4>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex, last);             \
+    else                                                                                                       \
+        f32_substep4_fixed<SHAPE, R, DD, 8>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex, last);
+    switch (D) {
+    case 0: GBS_FIXED(0) break;
+    case 1: GBS_FIXED(1) break;
+    case 2: GBS_FIXED(2) break;
+    default: GBS_FIXED(3) break;
+    }
+#undef GBS_FIXED
+}
+
 // Persistent form: CTA b processes tiles b, b + gridDim.x, ...; while it
 // computes one tile it prefetches the next into the other staging buffer
 // with cp.async, so the FMA pipe never waits for a synchronous load phase.
@@ -493,6 +601,19 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && R <= 3) ? 3 : 2)
             const bool last = s == t;
             if constexpr (sizeof(T) == 4) {
                 const bool all_int = Y0 + lo >= R && Y0 + hiY <= Ey - R && X0 + lo >= R && X0 + hiX <= Ex - R;
+                if constexpr (R <= 2) {  // R = 3 would spill next to the rotation form
+                    if (all_int && ring.band == 0 && (cw & 3) == 0 && ch >= 8) {
+                        // strips of 8 rows, or of 4 when that tiles the region exactly
+                        const bool s4 = (ch & 7) != 0 && (ch & 3) == 0;
+                        f32_fixed_dispatch<SHAPE, R>((lo - R) & 3, s4, src, dst, out, wt, P, lo, hiY, hiX, Y0, X0,
+                                                     Ex, last);
+                        __syncthreads();
+                        T *tmp = src;
+                        src = dst;
+                        dst = tmp;
+                        continue;
+                    }
+                }
                 switch ((lo - R) & 3) {  // offset of the first window within its 16-byte chunk
                 case 0:
                     f32_substep4<SHAPE, R, 0>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ey, Ex, last, all_int,

@@ -1191,8 +1191,15 @@ stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, 
         case STENCIL_PREC_TF32: s = launch_tc2d_ws<tcs::P_TF32>(p, in, out, t, st); break;
         case STENCIL_PREC_TF32X3: s = launch_tc2d_ws<tcs::P_TF32X3>(p, in, out, t, st); break;
         case STENCIL_PREC_BF16X3: s = launch_tc2d<tcs::P_BF16X3, 8>(p, in, out, t, st); break;
-        case STENCIL_PREC_F16: s = launch_tc2d_wsh<tcs::P_F16>(p, in, out, t, st); break;
-        case STENCIL_PREC_F16X3: s = launch_tc2d_wsh<tcs::P_F16X3>(p, in, out, t, st); break;
+        case STENCIL_PREC_F16:
+        case STENCIL_PREC_F16X3: {
+            // the wide form where its operands fit, else N = 32 / 16 tiles
+            const bool split = p.precision == STENCIL_PREC_F16X3;
+            if (tc_wide_nrows(p.pat.r, t, split) > 0) s = launch_wide_sweep(p, in, out, t, split, st);
+            else if (split) s = launch_tc2d_wsh<tcs::P_F16X3>(p, in, out, t, st);
+            else s = launch_tc2d_wsh<tcs::P_F16>(p, in, out, t, st);
+            break;
+        }
         default: return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: precision");
         }
     }
@@ -1207,10 +1214,12 @@ stencil_status read_device_error(int *flag)
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
     if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-    int vs = 0;
+    int vs = 0, vw = 0;
     stencil_status s = read_split_error(&vs);
     if (s != STENCIL_OK) return s;
-    *flag = v | vs;
+    s = read_wide_error(&vw);
+    if (s != STENCIL_OK) return s;
+    *flag = v | vs | vw;
     return STENCIL_OK;
 }
 

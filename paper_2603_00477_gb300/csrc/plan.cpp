@@ -169,8 +169,11 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
         g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
-    if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3))
-        g.n_tile = std::max(16, tc_wsh_ntile(shape, r, t, precision == STENCIL_PREC_F16X3));
+    if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3)) {
+        // the wide kernel: 128 output columns per MMA (M), else N = 32 / 16 tiles
+        const bool split = precision == STENCIL_PREC_F16X3;
+        g.n_tile = tc_wide_nrows(r, t, split) > 0 ? 128 : std::max(16, tc_wsh_ntile(shape, r, t, split));
+    }
     if (d == 2 && path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
         // mma.sp m16n8k16: 16 output columns per block, logical K 16
         SpLayout L = sp_layout_2d(shape, r, t);
@@ -261,6 +264,7 @@ constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
 constexpr double kWorkerF16 = 2.20;        // tc2d_wsh F16: staging, exponent, conversion, epilogue
 constexpr double kWorkerF16x3 = 2.40;      // tc2d_wsh F16x3: + the lo parts
 constexpr double kMmaCyclesWsh = 110.0;    // tc2d_wsh: its MMAs share shared memory with the conversion
+constexpr double kWorkerWide = 0.40;       // tc2d_wide: two load passes, conversion, epilogue (estimate)
 // tc2d_sweep BF16x3 runs one tile per CTA with several CTAs per SM, whose
 // MMAs interleave: 2.65 cycles per output plus 47.6 per MMA of an output
 // (fitted to Box-2D2R at t = 1..4 within 10 %)
@@ -300,6 +304,18 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
         const double mma = blocks * S / (128.0 * 16.0) * kMmaCycles;
         per_out = std::max(mma, kWorkerSplit);
+    } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) &&
+               tc_wide_nrows(r, t, prec == STENCIL_PREC_F16X3) > 0) {
+        // tc2d_wide: per tile of 128 columns x nr rows, one MMA (M = 128,
+        // N = nr, K = 16) per (line, K block) and product, each costing
+        // max(kMmaCycles, its arithmetic at 4096 FP16 MACs per cycle)
+        const int nr = tc_wide_nrows(r, t, prec == STENCIL_PREC_F16X3);
+        const TcLines L = tc_lines_2d(shape, r, t, 128, 16);
+        double blocks = 0;
+        for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
+        const double products = prec == STENCIL_PREC_F16 ? 1.0 : 3.0;
+        const double mma = blocks * products / (128.0 * nr) * std::max(kMmaCycles, 128.0 * nr * 16 / 4096.0);
+        per_out = std::max(mma, kWorkerWide);
     } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3)) {
         const int n = tc_wsh_ntile(shape, r, t, prec == STENCIL_PREC_F16X3);
         if (n == 0) return 0;
@@ -438,10 +454,12 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                         c.tile[2] = 16 * split_nacc(t * r, slices);
                     }
                     if (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
-                        const int tn = tc_wsh_ntile(shape, r, t, prec == STENCIL_PREC_F16X3);
-                        if (tn == 0) continue;  // the tile does not fit
-                        c.tile[1] = 128;
-                        c.tile[2] = 2 * tn;
+                        const bool split = prec == STENCIL_PREC_F16X3;
+                        const int nr = tc_wide_nrows(r, t, split);
+                        const int tn = tc_wsh_ntile(shape, r, t, split);
+                        if (nr == 0 && tn == 0) continue;  // the tile does not fit
+                        c.tile[1] = nr > 0 ? nr : 128;
+                        c.tile[2] = nr > 0 ? 128 : 2 * tn;
                     }
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec, slices), P_cu,

@@ -109,6 +109,43 @@ inline int tc_wsh_ntile(int shape, int r, int t, bool split)
     return 0;
 }
 
+// Wide FP16 kernel (tc2d_wide): the Toeplitz factor of line a is the A
+// operand over M = 128 output columns (stored in reverse order, so that
+// A[m'][k] depends on k + m' only) and K = 16 nkb window columns,
+// nkb = ceil((128 + 2R) / 16); the input tile is the B operand over N = nr
+// output rows.  Line a's A operand for every K block is read from one strip
+// of 2 nkb + 15 core matrices (128 bytes each), non-zero only in core
+// matrices 15 .. (127 + 2R) / 8, so consecutive lines' strips are placed
+// max(2 nkb, (127 + 2R) / 8 + 1) core matrices apart and overlap in zeros.
+struct WideGeom {
+    int nkb, strip_len, delta, hs;
+    size_t strip_bytes, in_bytes, smem;
+};
+
+inline WideGeom tc_wide_geom(int R, int nr, bool split)
+{
+    WideGeom g;
+    g.nkb = (128 + 2 * R + 15) / 16;
+    g.strip_len = 2 * g.nkb + 15;
+    g.delta = std::max(2 * g.nkb, (127 + 2 * R) / 8 + 1);
+    g.hs = (nr + 2 * R) | 1;  // odd chunk-column height: conflict-free staging stores
+    g.strip_bytes = (size_t)(2 * R * g.delta + g.strip_len) * 128;
+    g.in_bytes = (size_t)(2 * g.nkb) * g.hs * 16;
+    // 1 KB header, weight strips (hi, lo), two input buffers (hi, lo)
+    g.smem = 1024 + (g.strip_bytes + 2 * g.in_bytes) * (split ? 2 : 1);
+    return g;
+}
+
+// Output rows per tile (MMA N) of the wide kernel: the largest of 256, 128
+// and 64 whose operands fit in 227 KB; 0 if none does (R > 12 or no fit).
+inline int tc_wide_nrows(int r, int t, bool split)
+{
+    if (t * r > 12) return 0;
+    for (int nr : {256, 128, 64})
+        if (tc_wide_geom(t * r, nr, split).smem <= 227 * 1024) return nr;
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // 2:4-structured sparse form (paper Sec. 4.3), TF32 1:2 on mma.sp m16n8k16.
 //

@@ -72,6 +72,14 @@ CASES_2D = [
     ("box", 5, (33, 70), 4, 3, "f32", None),
     ("star", 4, (200, 90), 5, 2, "f64", "16x32"),       # small tiles, many CTAs
     ("box", 2, (7, 3), 4, 4, "f32", None),              # extent below r*t
+    # FP32, r <= 2, grids of several whole interior tiles: the fixed-strip
+    # sub-step (strips of 8 and 4 rows, all four window phases over t)
+    ("box", 1, (300, 700), 5, 3, "f32", None),
+    ("star", 1, (260, 600), 6, 2, "f32", None),
+    ("star", 2, (300, 520), 7, 4, "f32", None),
+    ("box", 2, (200, 600), 5, 2, "f32", None),
+    ("box", 2, (170, 530), 3, 3, "f32", "42x128"),     # strips overlap (ch not a multiple of 4)
+    ("box", 1, (99, 1030), 2, 1, "f32", None),
 ]
 
 
@@ -210,6 +218,28 @@ def test_config_box2d3r_16384_sampled(torch, t):
         ref = oracle.run_region("box", 2, 3, w, dims, u, 100, lo, hi)
         got = y[lo[0] + 3:hi[0] + 3, lo[1] + 3:hi[1] + 3].cpu().numpy()
         assert oracle.rel_linf(got, ref) <= 1e-12, (lo, hi)
+    plan.close()
+    del x, y
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("t", [1, 2, 3, 4])
+def test_config_box2d2r_f32_16384_cuda_core_sampled(torch, t):
+    """Box-2D2R FP32 on 16384^2 (sine-mode field), 20 steps on CUDA cores:
+    sampled outputs against the oracle's dependency-cone evaluation."""
+    dims = (16384, 16384)
+    w, u = inputs.problem("box", 2, 2, dims, seed=4, dtype=np.float32, field="sine")
+    plan = B.Plan("box", 2, 2, w, "f32", dims, t)
+    plan.set_option("path", "cuda_core")
+    x = torch.from_numpy(u).cuda()
+    y = torch.empty_like(x)
+    plan.run(x, y, 20)
+    torch.cuda.synchronize()
+    u64 = u.astype(np.float64)
+    for lo, hi in SAMPLE_BOXES_2D:
+        ref = oracle.run_region("box", 2, 2, w, dims, u64, 20, lo, hi)
+        got = y[lo[0] + 2:hi[0] + 2, lo[1] + 2:hi[1] + 2].cpu().numpy()
+        assert oracle.rel_linf(got, ref) <= TOL["f32"], (lo, hi)
     plan.close()
     del x, y
     torch.cuda.empty_cache()

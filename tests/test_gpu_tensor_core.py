@@ -76,6 +76,12 @@ CASES = [
     ("box", 3, (140, 75), 5, 2, "f32", "f16x3"),       # R = 6: N = 16
     ("star", 1, (128, 128), 7, 4, "f32", "f16x3"),
     ("box", 1, (5, 7), 3, 3, "f32", "f16"),            # grid smaller than the band
+    # the wide FP16 kernel with more tiles than SMs (each persistent CTA
+    # cycles through both operand buffers and accumulators several times)
+    ("box", 2, (4000, 4000), 6, 2, "f32", "f16"),       # 16 x 32 tiles of 256 x 128
+    ("star", 3, (3000, 3500), 8, 4, "f32", "f16"),      # R = 12: 128-row tiles
+    ("box", 1, (2000, 3001), 9, 4, "f32", "f16x3"),     # R = 4, 128-row tiles, unaligned rows
+    ("box", 2, (700, 900), 4, 4, "f32", "f16x3"),       # R = 8: 64-row tiles
 ]
 
 
