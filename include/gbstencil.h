@@ -243,8 +243,13 @@ stencil_status stencil_run(stencil_plan *plan, const void *in, void *out, int64_
 /* stencil_run from host memory (no counterpart in the paper).
  * Same computation from host memory: copies host_in to the device,
  * runs, copies the result to host_out, and synchronises `stream` before
- * returning.  Needs stencil_plan_workspace_bytes(plan, 1) of workspace.
- * Pinned host memory gives full copy bandwidth. */
+ * returning (it also waits for the sweeps before the copy back).  Needs
+ * stencil_plan_workspace_bytes(plan, 1) of workspace.  Pinned host memory
+ * gives full copy bandwidth.  Right before each copy the calling thread reads
+ * one byte per 4 KiB page of that host buffer: on Grace-based GB300 machines
+ * the copy engine reads host pages the CPU has left alone for a few seconds
+ * at ~5-16 GB/s instead of ~210 GB/s, and the touch (~3 ms per GB) restores
+ * the fast rate.  Both buffers must therefore be readable by the CPU. */
 stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *host_out,
                                 int64_t steps, stencil_stream_t stream);
 
@@ -252,12 +257,10 @@ stencil_status stencil_run_host(stencil_plan *plan, const void *host_in, void *h
  * counterpart in the paper).  Allocates `bytes` (rounded up to 2 MiB) of
  * zero-filled host memory aligned to 2 MiB, advised to use transparent huge
  * pages and registered with CUDA (portable, so copies from it run at full
- * speed).  GPU reads of page-locked memory mapped with 4 KiB pages drop to
- * ~10 GB/s on Grace-based GB300 machines once their translations have gone
- * cold (after seconds of HBM-bound kernels); with 2 MiB pages they stay near
- * ~110 GB/s cold and ~210 GB/s warm.  The memory belongs to the caller until
- * stencil_host_free.  INVALID_ARG for a null ptr or bytes == 0; OOM if the
- * mapping fails; CUDA if the registration fails (nothing is left mapped). */
+ * speed, ~210 GB/s host to device on GB300).  The memory belongs to the
+ * caller until stencil_host_free.  INVALID_ARG for a null ptr or
+ * bytes == 0; OOM if the mapping fails; CUDA if the registration fails
+ * (nothing is left mapped). */
 stencil_status stencil_host_alloc(void **ptr, size_t bytes);
 
 /* Release memory from stencil_host_alloc (null is a no-op); INVALID_ARG for

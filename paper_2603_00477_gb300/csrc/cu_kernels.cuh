@@ -1055,5 +1055,209 @@ __global__ void __launch_bounds__(kThreads, 2)
     cp_async_wait_group<0>();
 }
 
+
+// ---------------------------------------------------------------------------
+// 3-D, t = 1, FP32: z-marching with rotating partial sums.
+// ---------------------------------------------------------------------------
+// A work item is a 64-column x BY-row tile and a run of cz output planes.
+// The CTA stages ONE input plane at a time (a ring of kRotNPL planes keeps the
+// next ones in flight with cp.async) and adds it, once, into every output
+// plane it touches: input plane ip contributes its 2-D slice w(oz, ., .) to
+// output plane ip - R - oz for oz in [-R, R], so each thread keeps the partial
+// sums of its 4 columns x RPT rows for 2R+1 output planes in registers
+// (slots rotate with the plane index; the plane loop is unrolled by 2R+1, so
+// every slot and weight index is a compile-time constant).  Output plane oq
+// is complete after input plane oq + 2R and is stored from its slot.  Input
+// planes of the first and last 2R of a run also add into slots of outputs
+// outside the run; those slots are cleared, never stored.
+// Staged planes hold columns X0 - 4 .. X0 + 67 (tiles start R mod 4 columns
+// left of the interior, so the window and every thread's 4 output columns
+// are 16-byte aligned): a thread's taps need the 16-byte chunks tx, tx+1,
+// tx+2 of a row; rows that only the centre column touches (star stencils)
+// need chunk tx+1 alone.  Each staged value is read from shared memory once
+// per (row, thread) instead of once per output plane.
+constexpr int kRotNPL = 4;   // ring planes: the one computed and three in flight
+constexpr int kRotPW = 72;   // staged columns (64 + 2 x 4)
+
+template <int SHAPE, int R>
+__host__ __device__ constexpr int rot_rows_per_thread()
+{
+    return R <= 2 ? 2 : 1;
+}
+
+template <int SHAPE, int R>
+__host__ __device__ constexpr size_t rot_smem_bytes()
+{
+    return (size_t)kRotNPL * (16 * rot_rows_per_thread<SHAPE, R>() + 2 * R) * kRotPW * sizeof(float);
+}
+
+// Does staged row j (0 .. RPT + 2R - 1) of a thread need more than the
+// centre chunk?  (Yes if some output row i takes it as its own row, oy = 0,
+// or the stencil is a box.)
+template <int SHAPE, int R, int RPT>
+__host__ __device__ constexpr bool rot_full_row(int j)
+{
+    return SHAPE == 0 || (j >= R && j < R + RPT);
+}
+
+template <int SHAPE, int R>
+__global__ void __launch_bounds__(kThreads, 3)
+    cu3d_rot(const float *__restrict__ in, float *__restrict__ out,
+             const __grid_constant__ Weights<float, Taps<SHAPE, 3, R>::K> wt, int64_t Ez, int64_t Ey, int64_t Ex,
+             int tiles_x, int tiles_y, int nitems, int cz, int xs)
+{
+    constexpr int RPT = rot_rows_per_thread<SHAPE, R>(), BY = 16 * RPT, BX = 64;
+    constexpr int PH = BY + 2 * R, PW = kRotPW, PE = PH * PW, NS = 2 * R + 1;
+    constexpr int NCH = PW / 4;  // 16-byte chunks per staged row
+    static_assert(R <= 3, "the plane loop unrolls (2R+1)-fold: radii up to 3");
+    extern __shared__ __align__(16) float ring[];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t nz = Ez - 2 * R, ny = Ey - 2 * R, nx = Ex - 2 * R;
+    const bool vec = (Ex & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    const bool vst = (Ex & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int bx = item % tiles_x, by = (item / tiles_x) % tiles_y, bz = item / (tiles_x * tiles_y);
+        // stored coordinates of the item's first output (column X0 may lie in the halo)
+        const int64_t Z0 = R + (int64_t)bz * cz, Y0 = R + (int64_t)by * BY, X0 = R + (int64_t)bx * BX - xs;
+        const int64_t rem = nz - (Z0 - R);
+        const int nzo = (int)(rem < cz ? rem : cz);
+        const int nin = nzo + 2 * R;
+        const int64_t zfirst = Z0 - R;
+        // items whose staged rows and columns lie inside the stored plane (all
+        // but the edges): 32-bit in-plane offsets, no per-chunk tests
+        const bool inner = vec && Y0 - R >= 0 && Y0 - R + PH <= Ey && X0 - 4 >= 0 && X0 - 4 + PW <= Ex;
+        const int ex32 = (int)Ex;                        // a stored row holds < 2^31 values
+        const int base_off = (int)((Y0 - R) * Ex + (X0 - 4));  // and a stored plane too
+        auto load_plane = [&](int ip) {
+            float *dst = ring + (size_t)(ip & (kRotNPL - 1)) * PE;
+            const int64_t gz = zfirst + ip;
+            const bool zok = gz >= 0 && gz < Ez;
+            if (inner && zok) {
+                const float *src = in + gz * Ey * Ex + base_off;
+                for (int e = tid; e < PH * NCH; e += kThreads) {
+                    const int row = e / NCH, ch = e - (e / NCH) * NCH;
+                    cp_async_elem<16>(dst + row * PW + 4 * ch, src + row * ex32 + 4 * ch, true);
+                }
+                return;
+            }
+            for (int e = tid; e < PH * NCH; e += kThreads) {
+                const int row = e / NCH, ch = e - (e / NCH) * NCH;
+                const int64_t gy = Y0 - R + row, gx = X0 - 4 + 4 * ch;
+                const bool rok = zok && gy >= 0 && gy < Ey;
+                const float *src = in + ((rok ? gz : 0) * Ey + (rok ? gy : 0)) * Ex;
+                float *d = dst + row * PW + 4 * ch;
+                if (vec) {
+                    // gx is a multiple of 4 and so is Ex: the chunk is wholly in or out
+                    const bool ok = rok && gx >= 0 && gx < Ex;
+                    cp_async_elem<16>(d, ok ? src + gx : in, ok);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const bool ok = rok && gx + c >= 0 && gx + c < Ex;
+                        cp_async_elem<4>(d + c, ok ? src + gx + c : in, ok);
+                    }
+                }
+            }
+        };
+        __syncthreads();  // the previous item's reads of the ring are done
+#pragma unroll
+        for (int k = 0; k < kRotNPL - 1; ++k) {
+            if (k < nin) load_plane(k);
+            cp_async_commit();
+        }
+        float acc[NS][RPT][4];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) acc[s][i][0] = acc[s][i][1] = acc[s][i][2] = acc[s][i][3] = 0.0f;
+        const int64_t gy0 = Y0 + ty * RPT, gx0 = X0 + 4 * tx;
+        // this thread's output quads: offset within a stored plane, row inside
+        // the interior, and which columns are interior
+        const bool qfull = gx0 >= R && gx0 + 3 - R < nx;
+        unsigned cmask = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmask |= (gx0 + c >= R && gx0 + c - R < nx) ? (1u << c) : 0u;
+        const int nrow_ok = (int)min((int64_t)RPT, ny + R - gy0);  // rows of the thread inside the interior
+        const int ooff0 = (int)(gy0 * Ex + gx0);                  // offset within a stored plane
+        for (int base = 0; base < nin; base += NS) {
+#pragma unroll
+            for (int u = 0; u < NS; ++u) {
+                const int ip = base + u;
+                if (ip >= nin) break;
+                // plane ip + NPL - 1 goes into the slot plane ip - 1 used (read before the last barrier)
+                if (ip + kRotNPL - 1 < nin) load_plane(ip + kRotNPL - 1);
+                cp_async_commit();
+                cp_async_wait_group<kRotNPL - 1>();  // plane ip has landed
+                __syncthreads();
+                const float *pl = ring + (size_t)(ip & (kRotNPL - 1)) * PE + (ty * RPT) * PW + 4 * tx;
+#pragma unroll
+                for (int j = 0; j < RPT + 2 * R; ++j) {
+                    const float *rowp = pl + j * PW;
+                    float v[12];
+                    const float4 c1 = *reinterpret_cast<const float4 *>(rowp + 4);
+                    v[4] = c1.x;
+                    v[5] = c1.y;
+                    v[6] = c1.z;
+                    v[7] = c1.w;
+                    if (rot_full_row<SHAPE, R, RPT>(j)) {
+                        const float4 c0 = *reinterpret_cast<const float4 *>(rowp);
+                        const float4 c2 = *reinterpret_cast<const float4 *>(rowp + 8);
+                        v[0] = c0.x;
+                        v[1] = c0.y;
+                        v[2] = c0.z;
+                        v[3] = c0.w;
+                        v[8] = c2.x;
+                        v[9] = c2.y;
+                        v[10] = c2.z;
+                        v[11] = c2.w;
+                    }
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i) {
+                        const int oy = j - i - R;
+                        if (oy < -R || oy > R) continue;
+#pragma unroll
+                        for (int oz = -R; oz <= R; ++oz) {
+                            const int slot = ((u - R - oz) % NS + 2 * NS) % NS;
+#pragma unroll
+                            for (int ox = -R; ox <= R; ++ox) {
+                                const int k = tap_index<SHAPE, 3, R>(oz, oy, ox);
+                                if (k >= 0) {
+#pragma unroll
+                                    for (int c = 0; c < 4; ++c)
+                                        acc[slot][i][c] = fmaf(wt.w[k], v[4 + c + ox], acc[slot][i][c]);
+                                }
+                            }
+                        }
+                    }
+                }
+                // output plane ip - 2R is complete (slot (u + 1) mod NS)
+                const int oq = ip - 2 * R;
+                const int sd = (u + 1) % NS;
+                if (oq >= 0 && oq < nzo) {
+                    float *obase = out + (Z0 + oq) * Ey * Ex;
+#pragma unroll
+                    for (int i = 0; i < RPT; ++i) {
+                        if (i >= nrow_ok) continue;
+                        float *o = obase + ooff0 + i * ex32;
+                        if (vst && qfull) {
+                            *reinterpret_cast<float4 *>(o) =
+                                make_float4(acc[sd][i][0], acc[sd][i][1], acc[sd][i][2], acc[sd][i][3]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if ((cmask >> c) & 1u) o[c] = acc[sd][i][c];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) acc[sd][i][0] = acc[sd][i][1] = acc[sd][i][2] = acc[sd][i][3] = 0.0f;
+                __syncthreads();  // the slot of plane ip is free for plane ip + NPL
+            }
+        }
+    }
+    cp_async_wait_group<0>();
+}
+
 }  // namespace cu
 }  // namespace gbs

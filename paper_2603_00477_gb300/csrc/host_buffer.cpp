@@ -1,14 +1,13 @@
-// host_buffer.cpp -- page-locked host buffers backed by 2 MiB pages, for the
-// host copies of stencil_run_host (a library service; the paper has none).
+// host_buffer.cpp -- page-locked host buffers for the host copies of
+// stencil_run_host (a library service; the paper has none).
 //
-// On the GB300 machines this library targets (Grace CPU, coherent C2C link),
-// GPU reads of page-locked host memory mapped with 4 KiB pages fall to
-// ~10 GB/s once the pages' translations have gone cold (after a few seconds
-// of kernels streaming HBM), against ~210 GB/s warm; the same memory mapped
-// with 2 MiB pages reads at ~110 GB/s cold.  stencil_host_alloc maps
-// anonymous memory aligned to 2 MiB, asks the kernel for transparent huge
-// pages (madvise(MADV_HUGEPAGE)), touches every page and registers the range
-// with CUDA (cudaHostRegister, portable).
+// stencil_host_alloc maps anonymous memory aligned to 2 MiB, asks the kernel
+// for transparent huge pages (madvise(MADV_HUGEPAGE): fewer translations for
+// the copy engine), touches every page and registers the range with CUDA
+// (cudaHostRegister, portable).  Whatever the page size, GPU copies of host
+// pages the CPU has not touched for a few seconds run slowly on Grace-based
+// machines; stencil_run_host touches its buffers right before each copy
+// (run.cu).
 #include <sys/mman.h>
 
 #include <cstdint>

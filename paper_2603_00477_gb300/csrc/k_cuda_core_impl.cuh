@@ -119,10 +119,56 @@ stencil_status launch3d_stream(const Plan &p, const void *in, void *out, cudaStr
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu3d_stream launch");
 }
 
+// 3-D, t = 1, FP32: z-marching with rotating partial sums (cu3d_rot).  The
+// run of output planes per work item, cz, is chosen so that the items fill
+// whole rounds of the resident CTAs: the time is ~ rounds x (cz + 2R) planes.
+template <int SHAPE, int R>
+stencil_status launch3d_rot(const Plan &p, const void *in, void *out, cudaStream_t st)
+{
+    using Wt = cu::Weights<float, cu::Taps<SHAPE, 3, R>::K>;
+    Wt wt;
+    for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (float)p.w[k];
+    const size_t smem = cu::rot_smem_bytes<SHAPE, R>();
+    auto kern = cu::cu3d_rot<SHAPE, R>;
+    stencil_status s = ensure_smem((const void *)kern, smem);
+    if (s != STENCIL_OK) return s;
+    int occ = 0;
+    s = occupancy((const void *)kern, cu::kThreads, smem, &occ);
+    if (s != STENCIL_OK) return s;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int BY = 16 * cu::rot_rows_per_thread<SHAPE, R>(), BX = 64, xs = R % 4;
+    const int64_t nz = p.dims[0], tyy = (p.dims[1] + BY - 1) / BY, txx = (p.dims[2] + xs + BX - 1) / BX;
+    const int64_t cols = tyy * txx, slots = (int64_t)std::max(1, occ) * std::max(1, sms);
+    int64_t cz = nz, best = -1;
+    for (int64_t m = 1; m <= std::min<int64_t>(nz, 512); m++) {
+        const int64_t c = (nz + m - 1) / m, items = ((nz + c - 1) / c) * cols;
+        const int64_t cost = (items + slots - 1) / slots * (c + 2 * R);
+        if (best < 0 || cost < best) {
+            best = cost;
+            cz = c;
+        }
+    }
+    const int64_t items = ((nz + cz - 1) / cz) * cols;
+    if (items > 0x7fffffff || cz > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
+    const unsigned grid = (unsigned)std::min<int64_t>(items, slots);
+    kern<<<grid, cu::kThreads, smem, st>>>((const float *)in, (float *)out, wt, p.ext[0], p.ext[1], p.ext[2],
+                                           (int)txx, (int)tyy, (int)items, (int)cz, xs);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "cu3d_rot launch");
+}
+
 template <typename T, int SHAPE, int R>
 stencil_status launch3d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
-    if (t == 1) return launch3d_stream<T, SHAPE, R>(p, in, out, st);
+    if (t == 1) {
+        // FP32 star r <= 3 and box r = 1: rotating partial sums; the rest streams
+        if constexpr (sizeof(T) == 4 && ((SHAPE == 1 && R <= 3) || (SHAPE == 0 && R == 1)))
+            return launch3d_rot<SHAPE, R>(p, in, out, st);
+        return launch3d_stream<T, SHAPE, R>(p, in, out, st);
+    }
     using Wt = cu::Weights<T, cu::Taps<SHAPE, 3, R>::K>;
     Wt wt;
     for (int k = 0; k < cu::Taps<SHAPE, 3, R>::K; k++) wt.w[k] = (T)p.w[k];

@@ -28,6 +28,7 @@
 // All write interior points farther than (t-1) r from the boundary only:
 // nearer points would need the halo re-imposed between the fused steps; the
 // CUDA-core band kernel computes them stepwise.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -49,12 +50,14 @@ constexpr int kTcMaxR = 12;
 constexpr int kTcMaxLines = 2 * kTcMaxR + 1;
 
 struct TcParams {
+    CUtensorMap tmap;  // tc2d_ws with tma: the input grid as a 2-D FP32 tensor, box 4 x (128 + 2R)
     double w[kTcMaxLines * kTcMaxLines];  // composite w^(t), (2R+1) x (2R+1), row-major
     unsigned char kb_lo[kTcMaxLines], kb_hi[kTcMaxLines];
     int R, rh, band, nkb, hs, nch;
     int debug_unmet;  // test hook: first wait on an mbarrier phase that never completes
     int vec16;        // tc2d_ws: stage 16-byte chunks (stored rows are 16-byte multiples)
     int xshift;       // tc2d_ws: tiles start xshift columns left of column 0 (aligned windows)
+    int tma;          // tc2d_ws: stage tiles with TMA (one box per 16-byte chunk column)
     int ew;           // tc2d_wsh: the composite weights are scaled by 2^-ew (|w| 2^-ew < 1)
     int64_t Ey, Ex;
 };
@@ -324,6 +327,7 @@ __global__ void __launch_bounds__(288, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + 16);   // [2]
     uint64_t *done = reinterpret_cast<uint64_t *>(smem + 32);   // [2]
     uint64_t *freeb = reinterpret_cast<uint64_t *>(smem + 48);  // [2]
+    uint64_t *tmab = reinterpret_cast<uint64_t *>(smem + 64);   // [2] TMA copies of a buffer landed
     const int R = p.R, HS = p.hs, NCH = p.nch, nkb = p.nkb;
     const int lines = 2 * R + 1;
     const uint32_t a_bytes = (uint32_t)NCH * HS * 16;
@@ -344,6 +348,7 @@ __global__ void __launch_bounds__(288, 1)
             mbar_init(&full[b], 256);   // all eight worker warps
             mbar_init(&done[b], 1);
             mbar_init(&freeb[b], 128);  // the four epilogue warps
+            mbar_init(&tmab[b], 1);     // thread 0's expect_tx arrival
         }
         fence_mbar_init();
     }
@@ -436,9 +441,23 @@ __global__ void __launch_bounds__(288, 1)
     } else {
         // ---------------- loaders / converters (warps 0-7), epilogue (warps 0-3) -----
         const int rows = TM + 2 * R, cols = NCH * E;
-        auto prefetch = [&](int id, float *dst) {
+        int tma_pending = -1;  // buffer whose TMA copies may still be in flight
+        auto prefetch = [&](int id, float *dst, int buf) {
             int64_t Y0, X0;
             origin(id, &Y0, &X0);
+            if (p.tma) {
+                // one box of 4 values x rows per 16-byte chunk column (X0 - R is a
+                // multiple of 4: every box starts on a 16-byte boundary); rows and
+                // chunks outside the grid arrive as zeros
+                if (tid == 0) {
+                    mbar_arrive_expect_tx(&tmab[buf], (uint32_t)(NCH * rows * 16));
+                    for (int c = 0; c < NCH; ++c)
+                        tma_load_2d(reinterpret_cast<unsigned char *>(dst) + (size_t)c * HS * 16, &p.tmap,
+                                    (int)(X0 - R) + 4 * c, (int)(Y0 - R), &tmab[buf]);
+                }
+                tma_pending = buf;
+                return;
+            }
             if (p.vec16) {
                 // one 16-byte copy per (row, chunk column); X0 - R is a multiple of 4,
                 // so each chunk lies wholly inside or wholly outside its row
@@ -511,16 +530,25 @@ __global__ void __launch_bounds__(288, 1)
         };
 
         int k = 0, prev = -1;
-        if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, Ahi[0]);
+        if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, Ahi[0], 0);
         cu::cp_async_commit();
         bool ok = true;
         for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++k) {
             const int b = k & 1;
-            cu::cp_async_wait_group<0>();
-            named_bar_sync(1, 256);
-            if (*(volatile int *)abort_flag) {
-                ok = false;
-                break;
+            if (p.tma) {
+                // buffer b's TMA copies have landed (phase = its use count)
+                if (!bounded_wait(&tmab[b], (k >> 1) & 1, kWaitCycles)) {
+                    ok = false;
+                    break;
+                }
+                tma_pending = -1;
+            } else {
+                cu::cp_async_wait_group<0>();
+                named_bar_sync(1, 256);
+                if (*(volatile int *)abort_flag) {
+                    ok = false;
+                    break;
+                }
             }
             // round to TF32 in place (and split off the lo part), 16 bytes at a time
             const int quads = (int)(a_bytes / 16);
@@ -544,7 +572,7 @@ __global__ void __launch_bounds__(288, 1)
             }
             // the next tile's loads go out first; the epilogue hides their latency
             const int nid = id + gridDim.x;
-            if (nid < ntiles) prefetch(nid, Ahi[b ^ 1]);
+            if (nid < ntiles) prefetch(nid, Ahi[b ^ 1], b ^ 1);
             cu::cp_async_commit();
             if (k >= 1 && warp < 4) {
                 epilogue(prev, tmem + (b ^ 1) * kSet);
@@ -563,6 +591,13 @@ __global__ void __launch_bounds__(288, 1)
         }
         cu::cp_async_wait_group<0>();
         if (!ok) atomicExch(abort_flag, 1);
+        // after an abort, TMA copies issued for the next tile may still be in
+        // flight: let them land (bounded) before the CTA's shared memory goes
+        if (tma_pending >= 0 && tid == 0) {
+            const unsigned long long t0 = clock64();
+            while (!mbar_try_wait(&tmab[tma_pending], (k >> 1) & 1) && clock64() - t0 < kWaitCycles) {
+            }
+        }
     }
     fence_before_thread_sync();
     __syncthreads();
@@ -1052,6 +1087,43 @@ stencil_status launch_tc2d(const Plan &p, const void *in, void *out, int t, cuda
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_sweep launch");
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (the library links only the runtime); null if unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// The FP32 input grid (Ey rows of Ex values, row pitch Ex * 4 bytes) as a 2-D
+// tensor map whose box is one 16-byte chunk column of a staged tile: 4 values
+// x rows.  Out-of-range elements load as zeros.  False if the map cannot be
+// made (the kernel then stages with cp.async).
+bool make_chunk_column_map(CUtensorMap *m, const void *in, int64_t Ey, int64_t Ex, int rows)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || rows > 256) return false;
+    const cuuint64_t dim[2] = {(cuuint64_t)Ex, (cuuint64_t)Ey};
+    const cuuint64_t stride[1] = {(cuuint64_t)Ex * 4};
+    const cuuint32_t box[2] = {4, (cuuint32_t)rows};
+    const cuuint32_t estride[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(in), dim, stride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int PREC, int TN_, int NACC>
 stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t, cudaStream_t st, bool *fits)
 {
@@ -1062,8 +1134,7 @@ stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t,
     stencil_status s = fill_params(p, t, TN_, 8, &tp, &L);
     if (s != STENCIL_OK) return s;
     const int R = tp.R;
-    tp.hs = TM + 2 * R;
-    if (tp.hs % 2 == 0) tp.hs += 1;
+    tp.hs = (TM + 2 * R + 7) / 8 * 8;  // chunk columns 128-byte aligned (TMA destinations)
     tp.nch = (TN_ * (NACC - 1) + L.kext) / 4;
     const bool split = PREC == P_TF32X3;
     const size_t a_bytes = (size_t)tp.nch * tp.hs * 16;
@@ -1082,6 +1153,8 @@ stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t,
     // window (tile start - R) begins on a 16-byte boundary
     tp.vec16 = (p.ext[2] % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
     tp.xshift = tp.vec16 ? (4 - R % 4) % 4 : 0;
+    // TMA staging needs 16-byte rows and aligned windows (vec16)
+    tp.tma = tp.vec16 && make_chunk_column_map(&tp.tmap, in, p.ext[1], p.ext[2], TM + 2 * R);
     const int64_t nty = (p.dims[1] + TM - 1) / TM, ntx = (p.ext[2] + tp.xshift + TX - 1) / TX;
     const int64_t ntiles = nty * ntx;
     if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
@@ -1190,12 +1263,16 @@ stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, 
         switch (p.precision) {
         case STENCIL_PREC_TF32: s = launch_tc2d_ws<tcs::P_TF32>(p, in, out, t, st); break;
         case STENCIL_PREC_TF32X3: s = launch_tc2d_ws<tcs::P_TF32X3>(p, in, out, t, st); break;
-        case STENCIL_PREC_BF16X3: s = launch_tc2d<tcs::P_BF16X3, 8>(p, in, out, t, st); break;
+        case STENCIL_PREC_BF16X3:
+            // the wide form where its operands fit, else the N = 8 synchronous kernel
+            if (tc_wide_nrows(p.pat.r, t, true) > 0) s = launch_wide_sweep(p, in, out, t, true, true, st);
+            else s = launch_tc2d<tcs::P_BF16X3, 8>(p, in, out, t, st);
+            break;
         case STENCIL_PREC_F16:
         case STENCIL_PREC_F16X3: {
             // the wide form where its operands fit, else N = 32 / 16 tiles
             const bool split = p.precision == STENCIL_PREC_F16X3;
-            if (tc_wide_nrows(p.pat.r, t, split) > 0) s = launch_wide_sweep(p, in, out, t, split, st);
+            if (tc_wide_nrows(p.pat.r, t, split) > 0) s = launch_wide_sweep(p, in, out, t, split, false, st);
             else if (split) s = launch_tc2d_wsh<tcs::P_F16X3>(p, in, out, t, st);
             else s = launch_tc2d_wsh<tcs::P_F16>(p, in, out, t, st);
             break;

@@ -1,5 +1,5 @@
-// k_wide.cu -- FP32 grids on the FP16 tensor cores with wide MMAs
-// (precisions f16 and f16x3): the Toeplitz (kernel-fusion) formulation of
+// k_wide.cu -- FP32 grids on the FP16 / BF16 tensor cores with wide MMAs
+// (precisions f16, f16x3 and bf16x3): the Toeplitz (kernel-fusion) formulation of
 // the paper's Sec. 2.2 with the roles of the two operands exchanged.
 //
 // On GB300 a tcgen05.mma of M = 128 costs a fixed ~90 cycles from one
@@ -23,22 +23,24 @@
 //
 // The input tile (NR + 2R rows x 16 nkb columns, FP32) is read twice from
 // global memory: once for its largest exponent, then again (from L2) to be
-// scaled by a power of two and converted to FP16 (hi, and lo = x - hi for
-// f16x3) in the chunk-column layout of k_tc.cu, where any 8 consecutive rows
+// scaled by a power of two and converted to FP16 or BF16 (hi, and lo = x - hi
+// for the 3-product forms) in the chunk-column layout of k_tc.cu, where any 8 consecutive rows
 // of a 16-byte chunk column form a K-major core matrix, so line a's B operand
 // is a descriptor at row offset a.  The weights are scaled by a power of two
 // likewise (hi and lo).  The scaled products accumulate in FP32 in TMEM
-// (lane = output column, column = output row); f16x3 adds hi*lo + lo*hi into
-// the same accumulator.  The epilogue undoes both scalings exactly.
+// (lane = output column, column = output row); the 3-product forms add
+// hi*lo + lo*hi into the same accumulator.  The epilogue undoes both scalings exactly.
 //
-// Persistent, warp specialised, one CTA per SM (672 threads): warps 0-15 load
+// Persistent, warp specialised, one CTA per SM (800 threads): warps 0-15 load
 // and convert the next tile into the other operand buffer, one thread of
-// warp 20 issues the MMAs into the other TMEM accumulator, warps 16-19 read
+// warp 24 issues the MMAs into the other TMEM accumulator, warps 16-23 read
 // the previous accumulator back (tcgen05.ld: one output column per thread,
-// consecutive output rows in consecutive registers) and store rows (32
-// consecutive columns per warp store).  Every wait is bounded.  Only
+// consecutive output rows in consecutive registers; two warps per TMEM lane
+// quarter, each half of the rows) and store rows (32 consecutive columns per
+// warp store).  Every wait is bounded.  Only
 // interior points farther than (t-1) r from the boundary are written; the
 // CUDA-core band kernel computes the others.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -67,9 +69,10 @@ constexpr int TM = 128;         // output columns per tile (MMA M)
 constexpr int KI = 16;          // K per instruction (kind::f16)
 constexpr int kLoadWarps = 16;                // warps 0-15
 constexpr int kLoaders = 32 * kLoadWarps;
-constexpr int kEpiWarp = kLoadWarps;          // warps 16-19 (TMEM lane quarters 0-3)
-constexpr int kMmaWarp = kLoadWarps + 4;      // warp 20
-constexpr int kThreads = 32 * (kLoadWarps + 5);
+constexpr int kEpiWarp = kLoadWarps;          // warps 16-23: TMEM lane quarter w % 4, half (w - 16) / 4
+constexpr int kEpiWarps = 8;
+constexpr int kMmaWarp = kLoadWarps + kEpiWarps;  // warp 24
+constexpr int kThreads = 32 * (kMmaWarp + 1);
 constexpr int kBatch = 8;                     // independent 16-byte loads in flight per loader thread
 constexpr int kHeader = 1024;
 constexpr unsigned long long kWaitCycles = 4ull << 30;       // ~2 s at 2 GHz
@@ -90,7 +93,44 @@ __device__ __forceinline__ float pow2f(int e)  // 2^e for -126 <= e <= 127
     return __int_as_float((e + 127) << 23);
 }
 
-template <bool SPLIT, int NR, int NKB>
+// Operand type: FP16 (11 significant bits) or BF16 (8 significant bits, the
+// range of FP32); packed conversions of two FP32 values and back.
+template <bool BF>
+struct Op;
+template <>
+struct Op<false> {
+    using T2 = __half2;
+    static constexpr uint32_t fmt = kFmtF16;
+    __device__ static T2 pack(float a, float b) { return __floats2half2_rn(a, b); }
+    __device__ static float2 unpack(T2 v) { return __half22float2(v); }
+    __device__ static uint16_t bits(double w)
+    {
+        const __half h = __double2half(w);
+        return *reinterpret_cast<const uint16_t *>(&h);
+    }
+    __device__ static double value(uint16_t b)
+    {
+        return (double)__half2float(*reinterpret_cast<const __half *>(&b));
+    }
+};
+template <>
+struct Op<true> {
+    using T2 = __nv_bfloat162;
+    static constexpr uint32_t fmt = kFmtBF16;
+    __device__ static T2 pack(float a, float b) { return __floats2bfloat162_rn(a, b); }
+    __device__ static float2 unpack(T2 v) { return __bfloat1622float2(v); }
+    __device__ static uint16_t bits(double w)
+    {
+        const __nv_bfloat16 h = __double2bfloat16(w);
+        return *reinterpret_cast<const uint16_t *>(&h);
+    }
+    __device__ static double value(uint16_t b)
+    {
+        return (double)__bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(&b));
+    }
+};
+
+template <bool SPLIT, int NR, int NKB, bool BF>
 __global__ void __launch_bounds__(kThreads, 1)
     tc2d_wide(const float *__restrict__ in, float *__restrict__ out, const __grid_constant__ WideParams p,
               int ntiles, int ntx)
@@ -125,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&full[b], kLoaders);
             mbar_init(&done[b], 1);
-            mbar_init(&accfree[b], 128);
+            mbar_init(&accfree[b], 32 * kEpiWarps);
             mbar_init(&maxb[b], kLoaders);
         }
         for (int s = 0; s < 4; ++s) mbar_init(&eub[s], 1);
@@ -146,9 +186,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (idx < 0 || idx > 2 * R) continue;
             const double wv = p.w[ai * lines + idx] * wsc;
             const uint32_t off = (uint32_t)(ai * p.delta + J) * 128 + ii * 16 + jj * 2;
-            const __half h = __double2half(wv);
-            *reinterpret_cast<__half *>(Whi + off) = h;
-            if (SPLIT) *reinterpret_cast<__half *>(Wlo + off) = __double2half(wv - (double)__half2float(h));
+            const uint16_t h = Op<BF>::bits(wv);
+            *reinterpret_cast<uint16_t *>(Whi + off) = h;
+            if (SPLIT) *reinterpret_cast<uint16_t *>(Wlo + off) = Op<BF>::bits(wv - Op<BF>::value(h));
         }
     }
     fence_proxy_async_smem();
@@ -176,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kMmaWarp) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = instr_desc(kFmtF16, TM, NR);
+            const uint32_t idesc = instr_desc(Op<BF>::fmt, TM, NR);
             const uint64_t a0 = smem_desc(smem_u32(Whi), 128, 128);
             const uint64_t dlo_a = (uint64_t)(strip_bytes >> 4);
             int k = 0;
@@ -238,26 +278,64 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (gx + 3 >= 0 && gx + 3 < Ex) v.w = __ldcg(g + gx + 3);
             return v;
         };
-        auto ex = [](float f) -> int { return (int)((__float_as_uint(f) >> 23) & 255u); };
+        // ask L2 for tile `id`'s input rows (one prefetch per 128 bytes, every
+        // address inside the stored array), so that both passes over it wait
+        // on L2 rather than DRAM latency
+        auto prefetch_l2 = [&](int id) {
+            int64_t Y0, X0;
+            origin(id, &Y0, &X0);
+            const int64_t gx_lo = max((int64_t)0, X0 - R), gx_hi = min(Ex, X0 - R + 16 * NKB);
+            if (gx_lo >= gx_hi) return;
+            const int lines = (int)((gx_hi - gx_lo + 31) / 32);
+            for (int e = tid; e < rows * lines; e += kLoaders) {
+                const int row = e / lines, l = e - (e / lines) * lines;
+                const int64_t gy = Y0 - R + row;
+                if (gy < 0 || gy >= Ey) continue;
+                const int64_t gx = min(gx_lo + 32 * (int64_t)l, gx_hi - 1);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(in + gy * Ex + gx));
+            }
+        };
         int k = 0;
         for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++k) {
             const int b = k & 1;
             int64_t Y0, X0;
             origin(id, &Y0, &X0);
-            // pass 1: the tile's largest biased exponent (kBatch loads in flight)
-            int mx = 0;
-            for (int i0 = tid; i0 < items; i0 += kBatch * kLoaders) {
-                float4 v[kBatch];
+            if (id + (int)gridDim.x < ntiles) prefetch_l2(id + gridDim.x);
+            // Interior tiles (the staged region inside the stored array, 16-byte
+            // rows): no per-load bounds tests; thread tid takes the float4 items
+            // i = tid + m kLoaders, whose (row, column) advance by a constant step.
+            const bool fast = vec16 && Y0 - R >= 0 && Y0 - R + rows <= Ey && X0 - R >= 0 &&
+                              X0 - R + 16 * NKB <= Ex;
+            const float *g0 = in + (Y0 - R) * Ex + (X0 - R);
+            constexpr int step_r = kLoaders / F4, step_c = kLoaders % F4;
+            auto load = [&](int i, int r, int c) -> float4 {
+                return fast ? __ldcg(reinterpret_cast<const float4 *>(g0 + (int64_t)r * Ex + 4 * c))
+                            : ld4(Y0, X0, i / F4, i % F4);
+            };
+            // pass 1: the tile's largest |x| as an unsigned integer (IEEE order), then its exponent
+            unsigned mxu = 0;
+            {
+                int row = tid / F4, c4 = tid % F4;
+                for (int i0 = tid; i0 < items; i0 += kBatch * kLoaders) {
+                    float4 v[kBatch];
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int i = i0 + u * kLoaders;
-                    v[u] = i < items ? ld4(Y0, X0, i / F4, i % F4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int u = 0; u < kBatch; ++u) {
+                        const int i = i0 + u * kLoaders;
+                        v[u] = i < items ? load(i, row, c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        row += step_r;
+                        c4 += step_c;
+                        if (c4 >= F4) {
+                            c4 -= F4;
+                            ++row;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u)
+                        mxu = max(mxu, max(max(__float_as_uint(v[u].x) & 0x7fffffffu, __float_as_uint(v[u].y) & 0x7fffffffu),
+                                           max(__float_as_uint(v[u].z) & 0x7fffffffu, __float_as_uint(v[u].w) & 0x7fffffffu)));
                 }
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u)
-                    mx = max(mx, max(max(ex(v[u].x), ex(v[u].y)), max(ex(v[u].z), ex(v[u].w))));
             }
-            mx = (int)__reduce_max_sync(0xffffffffu, (unsigned)mx);
+            const int mx = (int)(__reduce_max_sync(0xffffffffu, mxu) >> 23);
             if (lane == 0) wmax[b * kLoadWarps + warp] = mx;
             __syncwarp();
             mbar_arrive(&maxb[b]);
@@ -276,33 +354,41 @@ __global__ void __launch_bounds__(kThreads, 1)
                 eus[k & 3] = es;
                 mbar_arrive(&eub[k & 3]);
             }
-            // pass 2: scale, convert, store 4 FP16 values (8 bytes) per float4
+            // pass 2: scale, convert, store 4 FP16/BF16 values (8 bytes) per float4
             {
                 unsigned char *hi = ibase + b * in_bytes, *lo = hi + 2 * in_bytes;
+                int row = tid / F4, c4 = tid % F4;
                 for (int i0 = tid; i0 < items; i0 += kBatch * kLoaders) {
                     float4 vb[kBatch];
+                    int rr[kBatch], cc[kBatch];
 #pragma unroll
                     for (int u = 0; u < kBatch; ++u) {
                         const int i = i0 + u * kLoaders;
-                        vb[u] = i < items ? ld4(Y0, X0, i / F4, i % F4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        rr[u] = row;
+                        cc[u] = c4;
+                        vb[u] = i < items ? load(i, row, c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        row += step_r;
+                        c4 += step_c;
+                        if (c4 >= F4) {
+                            c4 -= F4;
+                            ++row;
+                        }
                     }
 #pragma unroll
                     for (int u = 0; u < kBatch; ++u) {
-                        const int i = i0 + u * kLoaders;
-                        if (i >= items) break;
-                        const int row = i / F4, c4 = i % F4;
+                        if (i0 + u * kLoaders >= items) break;
                         const float4 v = vb[u];
                         const float x0 = v.x * xs, x1 = v.y * xs, x2 = v.z * xs, x3 = v.w * xs;
-                        const __half2 h01 = __floats2half2_rn(x0, x1), h23 = __floats2half2_rn(x2, x3);
-                        const uint32_t off = (uint32_t)((c4 >> 1) * HS + row) * 16 + (uint32_t)(c4 & 1) * 8;
+                        const typename Op<BF>::T2 h01 = Op<BF>::pack(x0, x1), h23 = Op<BF>::pack(x2, x3);
+                        const uint32_t off = (uint32_t)((cc[u] >> 1) * HS + rr[u]) * 16 + (uint32_t)(cc[u] & 1) * 8;
                         uint2 hv;
                         hv.x = *reinterpret_cast<const uint32_t *>(&h01);
                         hv.y = *reinterpret_cast<const uint32_t *>(&h23);
                         *reinterpret_cast<uint2 *>(hi + off) = hv;
                         if (SPLIT) {
-                            const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
-                            const __half2 l01 = __floats2half2_rn(x0 - f01.x, x1 - f01.y);
-                            const __half2 l23 = __floats2half2_rn(x2 - f23.x, x3 - f23.y);
+                            const float2 f01 = Op<BF>::unpack(h01), f23 = Op<BF>::unpack(h23);
+                            const typename Op<BF>::T2 l01 = Op<BF>::pack(x0 - f01.x, x1 - f01.y);
+                            const typename Op<BF>::T2 l23 = Op<BF>::pack(x2 - f23.x, x3 - f23.y);
                             uint2 lv;
                             lv.x = *reinterpret_cast<const uint32_t *>(&l01);
                             lv.y = *reinterpret_cast<const uint32_t *>(&l23);
@@ -315,8 +401,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive(&full[b]);
         }
     } else {
-        // ---------------- epilogue (warps 16-19) ----------------
-        const int q = warp - kEpiWarp;  // TMEM lanes 32 q .. 32 q + 31
+        // ---------------- epilogue (warps 16-23) ----------------
+        // warp w reads TMEM lanes 32 q .. 32 q + 31 (q = w % 4, the lane quarter
+        // a warp may access) for the accumulator columns (output rows) of half h
+        const int q = (warp - kEpiWarp) & 3, h = (warp - kEpiWarp) >> 2;
         const int m = TM - 1 - (32 * q + lane);
         const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         int k = 0;
@@ -337,21 +425,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             origin(id, &Y0, &X0);
             const int64_t gx = X0 + m, ix = gx - rh;
             const bool colok = ix >= p.band && ix < nx - p.band;
+            // rows n of the tile written: interior rows iy = Y0 - rh + n in [band, ny - band)
+            const int n_lo = (int)max((int64_t)0, p.band - (Y0 - rh));
+            const int n_hi = (int)min((int64_t)NR, ny - p.band - (Y0 - rh));
             // out = acc 2^(ew - 15 - es), as two in-range powers of two
             const int e = p.ew - 15 - es, e1 = e / 2, e2 = e - e1;
             const float s1 = pow2f(max(-126, min(127, e1))), s2 = pow2f(max(-126, min(127, e2)));
-            for (int n0 = 0; n0 < NR; n0 += 16) {
+            float *o = out + Y0 * Ex + gx;
+            for (int n0 = h * (NR / 2); n0 < (h + 1) * (NR / 2); n0 += 16) {
                 uint32_t v[16];
                 __syncwarp();
                 tmem_ld_32x32b_x16(lane_base + (uint32_t)(b * NR + n0), v);
                 tmem_ld_wait();
-                const int64_t iy0 = Y0 + n0 - rh;
-                if (iy0 >= ny - p.band) break;  // rows below the written band
+                if (n0 >= n_hi) break;  // rows below the written band
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int64_t iy = iy0 + j;
-                    if (colok && iy >= p.band && iy < ny - p.band)
-                        out[(iy + rh) * Ex + gx] = __uint_as_float(v[j]) * s1 * s2;
+                    const int n = n0 + j;
+                    if (colok && n >= n_lo && n < n_hi) o[(int64_t)n * Ex] = __uint_as_float(v[j]) * s1 * s2;
                 }
             }
             fence_before_thread_sync();
@@ -372,7 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 namespace {
 
-template <bool SPLIT, int NR, int NKB>
+template <bool SPLIT, int NR, int NKB, bool BF>
 stencil_status launch_wide_n(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
     using namespace wide;
@@ -413,7 +503,7 @@ stencil_status launch_wide_n(const Plan &p, const void *in, void *out, int t, cu
     wp.Ex = p.ext[2];
     wp.vec16 = (p.ext[2] % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
     wp.xshift = wp.vec16 ? (4 - R % 4) % 4 : 0;  // (tile start - R) a multiple of 4
-    auto kern = tc2d_wide<SPLIT, NR, NKB>;
+    auto kern = tc2d_wide<SPLIT, NR, NKB, BF>;
     stencil_status s = ensure_smem((const void *)kern, g.smem);
     if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0;
@@ -431,19 +521,24 @@ stencil_status launch_wide_n(const Plan &p, const void *in, void *out, int t, cu
 
 }  // namespace
 
-stencil_status launch_wide_sweep(const Plan &p, const void *in, void *out, int t, bool split, cudaStream_t st)
+stencil_status launch_wide_sweep(const Plan &p, const void *in, void *out, int t, bool split, bool bf16,
+                                 cudaStream_t st)
 {
     const int nr = tc_wide_nrows(p.pat.r, t, split);
     const int nkb = tc_wide_geom(t * p.pat.r, nr > 0 ? nr : 64, split).nkb;  // 9 (R <= 8) or 10
     // the (N, K blocks) pairs tc_wide_nrows can pick
-    if (split) {  // hi and lo operands: N = 256 never fits
-        if (nr == 128 && nkb == 9) return launch_wide_n<true, 128, 9>(p, in, out, t, st);
-        if (nr == 64 && nkb == 9) return launch_wide_n<true, 64, 9>(p, in, out, t, st);
-        if (nr == 64 && nkb == 10) return launch_wide_n<true, 64, 10>(p, in, out, t, st);
-    } else {
-        if (nr == 256 && nkb == 9) return launch_wide_n<false, 256, 9>(p, in, out, t, st);
-        if (nr == 256 && nkb == 10) return launch_wide_n<false, 256, 10>(p, in, out, t, st);
-        if (nr == 128 && nkb == 10) return launch_wide_n<false, 128, 10>(p, in, out, t, st);
+    if (split && bf16) {  // hi and lo operands: N = 256 never fits
+        if (nr == 128 && nkb == 9) return launch_wide_n<true, 128, 9, true>(p, in, out, t, st);
+        if (nr == 64 && nkb == 9) return launch_wide_n<true, 64, 9, true>(p, in, out, t, st);
+        if (nr == 64 && nkb == 10) return launch_wide_n<true, 64, 10, true>(p, in, out, t, st);
+    } else if (split) {
+        if (nr == 128 && nkb == 9) return launch_wide_n<true, 128, 9, false>(p, in, out, t, st);
+        if (nr == 64 && nkb == 9) return launch_wide_n<true, 64, 9, false>(p, in, out, t, st);
+        if (nr == 64 && nkb == 10) return launch_wide_n<true, 64, 10, false>(p, in, out, t, st);
+    } else if (!bf16) {
+        if (nr == 256 && nkb == 9) return launch_wide_n<false, 256, 9, false>(p, in, out, t, st);
+        if (nr == 256 && nkb == 10) return launch_wide_n<false, 256, 10, false>(p, in, out, t, st);
+        if (nr == 128 && nkb == 10) return launch_wide_n<false, 128, 10, false>(p, in, out, t, st);
     }
     return fail(STENCIL_ERR_UNSUPPORTED, "wide FP16 tile does not fit in shared memory");
 }

@@ -30,11 +30,12 @@ stencil_status launch_split_sweep(const Plan &p, const void *in, void *out, int 
 // Read and clear the split kernel's own error word (part of read_device_error).
 stencil_status read_split_error(int *flag);
 
-// One fused sweep of depth t of an FP32 grid on the FP16 tensor cores with
-// wide MMAs (k_wide.cu; precision f16, or f16x3 when split), without the band
-// sweep.  STENCIL_ERR_UNSUPPORTED when its operands do not fit
-// (tc_wide_nrows == 0).
-stencil_status launch_wide_sweep(const Plan &p, const void *in, void *out, int t, bool split, cudaStream_t st);
+// One fused sweep of depth t of an FP32 grid on the FP16 / BF16 tensor cores
+// with wide MMAs (k_wide.cu; precision f16, f16x3 when split, bf16x3 when
+// split and bf16), without the band sweep.  STENCIL_ERR_UNSUPPORTED when its
+// operands do not fit (tc_wide_nrows == 0) or for BF16 without the split.
+stencil_status launch_wide_sweep(const Plan &p, const void *in, void *out, int t, bool split, bool bf16,
+                                 cudaStream_t st);
 
 // Read and clear the wide kernel's own error word (part of read_device_error).
 stencil_status read_wide_error(int *flag);

@@ -101,9 +101,11 @@ void cu_default_tile(const Plan &p, int t, int tile[3])
             if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
         }
     } else if (t == 1) {
-        // the streaming kernel: chunks of 64 planes of a (16 RPT) x 64 tile
+        // the streaming kernels: runs of planes (64 nominal; the rotating
+        // FP32 kernel sizes them to the resident CTAs) of a (16 RPT) x 64 tile
         tile[0] = 64;
         tile[1] = p.dtype == STENCIL_F64 ? 16 : 32;
+        if (p.dtype == STENCIL_F32 && p.pat.shape == STENCIL_STAR && R == 3) tile[1] = 16;
         tile[2] = 64;
     } else {
         tile[0] = 8;
@@ -169,6 +171,8 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
         g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
+    if (d == 2 && dtype == STENCIL_F32 && precision == STENCIL_PREC_BF16X3 && tc_wide_nrows(r, t, true) > 0)
+        g.n_tile = 128;  // the wide kernel (else the N = 8 synchronous kernel)
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3)) {
         // the wide kernel: 128 output columns per MMA (M), else N = 32 / 16 tiles
         const bool split = precision == STENCIL_PREC_F16X3;
@@ -304,12 +308,13 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
         const double mma = blocks * S / (128.0 * 16.0) * kMmaCycles;
         per_out = std::max(mma, kWorkerSplit);
-    } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) &&
-               tc_wide_nrows(r, t, prec == STENCIL_PREC_F16X3) > 0) {
+    } else if (p.dtype == STENCIL_F32 &&
+               (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3 || prec == STENCIL_PREC_BF16X3) &&
+               tc_wide_nrows(r, t, prec != STENCIL_PREC_F16) > 0) {
         // tc2d_wide: per tile of 128 columns x nr rows, one MMA (M = 128,
         // N = nr, K = 16) per (line, K block) and product, each costing
         // max(kMmaCycles, its arithmetic at 4096 FP16 MACs per cycle)
-        const int nr = tc_wide_nrows(r, t, prec == STENCIL_PREC_F16X3);
+        const int nr = tc_wide_nrows(r, t, prec != STENCIL_PREC_F16);
         const TcLines L = tc_lines_2d(shape, r, t, 128, 16);
         double blocks = 0;
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
@@ -452,6 +457,10 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                     if (prec == STENCIL_PREC_OZAKI) {
                         c.tile[1] = 128;
                         c.tile[2] = 16 * split_nacc(t * r, slices);
+                    }
+                    if (prec == STENCIL_PREC_BF16X3 && tc_wide_nrows(r, t, true) > 0) {
+                        c.tile[1] = tc_wide_nrows(r, t, true);
+                        c.tile[2] = 128;
                     }
                     if (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
                         const bool split = prec == STENCIL_PREC_F16X3;

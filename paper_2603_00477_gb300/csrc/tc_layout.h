@@ -68,11 +68,11 @@ inline TcLines tc_lines_2d(int shape, int r, int t, int n_tile, int k_inst)
 // MMA N (output columns per Toeplitz block) of the warp-specialised TF32 /
 // TF32x3 kernel: the widest of 32, 16, 8 whose operands fit in 227 KB of
 // shared memory -- B blocks (x2 split) plus double-buffered A tiles (hi, and
-// lo when split) of 128 + 2R rows (odd) by (NACC-1)*N + kext columns.
+// lo when split) of 128 + 2R rows (rounded up to 8) by (NACC-1)*N + kext columns.
 inline int tc_ws_ntile(int shape, int r, int t, bool split)
 {
     const int R = t * r;
-    const int hs = (128 + 2 * R) | 1;
+    const int hs = (128 + 2 * R + 7) / 8 * 8;  // chunk columns 128-byte aligned (TMA destinations)
     const int cand[3][2] = {{32, 2}, {16, 2}, {8, 4}};
     for (auto &c : cand) {
         const int n = c[0], nacc = c[1];

@@ -150,6 +150,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *mbar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
+// Arrive once on an mbarrier and add `bytes` to the transaction count its
+// current phase waits for (the bytes of the TMA copies that complete on it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// ---- TMA -------------------------------------------------------------------
+// Tiled 2-D copy of the box at element coordinates (x, y) of the tensor map
+// `tmap` (a __grid_constant__ kernel parameter) into shared memory at dst
+// (128-byte aligned); completes `bytes` of the transaction count of mbar.
+// Out-of-range elements are written as zeros.  x times the element size must
+// be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 // Barrier among a subset of the CTA's warps (named barrier `id`, `count`
 // threads, a multiple of 32).
 __device__ __forceinline__ void named_bar_sync(int id, int count)

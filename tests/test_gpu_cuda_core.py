@@ -107,6 +107,13 @@ CASES_3D = [
     ("box", 2, (12, 20, 37), 3, 1, "f64"),
     ("box", 2, (12, 20, 37), 4, 2, "f32"),
     ("star", 4, (13, 11, 33), 2, 1, "f32"),
+    # FP32, t = 1, rotating partial sums along z: ragged tiles, runs of planes
+    # per tile, unaligned rows (stored width not a multiple of 4), radius 3
+    ("star", 1, (70, 45, 130), 3, 1, "f32"),
+    ("star", 2, (41, 100, 201), 5, 1, "f32"),
+    ("star", 3, (40, 37, 90), 2, 1, "f32"),
+    ("box", 1, (150, 33, 70), 4, 1, "f32"),
+    ("box", 1, (3, 5, 7), 2, 1, "f32"),
     ("star", 3, (1, 5, 9), 3, 2, "f64"),
 ]
 

@@ -37,7 +37,7 @@ def test_toeplitz_times_im2col_equals_fused_sweep(shape, r, t, dtype, prec):
     lay, lo, hi, Bop = B.stencil_plan_tc_layout(p.handle, t)
     R, n, ki, nkb = lay["R"], lay["n_tile"], lay["k_inst"], lay["nkb"]
     assert R == t * r and lay["kext"] == nkb * ki and lay["kext"] >= n + 2 * R
-    dims = (30, 96)  # a multiple of every MMA N the layouts use (8, 16, 32)
+    dims = (30, 384)  # a multiple of every MMA N the layouts use (8, 16, 32, 128)
     rng = np.random.default_rng(3)
     u = rng.uniform(0, 1, size=(dims[0] + 2 * R, dims[1] + 2 * R + lay["kext"]))
     # im2col: window of output columns x0..x0+n-1 of row y for line a is
