@@ -228,17 +228,27 @@ def traffic_record(kernel_key):
 
 
 
-def kernel_name(info: dict, d: int, dtype: str) -> str:
-    """The sweep kernel a plan launches, from its path, precision and t."""
+def kernel_name(info: dict, d: int, dtype: str, shape: str = "box", r: int = 1) -> str:
+    """The sweep kernel a plan launches, from its stencil, path, precision,
+    tile and t (the rules of the library's launchers)."""
     if info["path"] == 1:
         if d == 2:
             return "cu2d_sweep"
-        return "cu3d_stream" if info["t"] == 1 else "cu3d_sweep"
+        if info["t"] != 1:
+            return "cu3d_sweep"
+        # FP32 star r <= 3 and box r = 1 take the rotating kernel
+        rot = dtype == "f32" and ((shape == "star" and r <= 3) or (shape == "box" and r == 1))
+        return "cu3d_rot" if rot else "cu3d_stream"
     if info["path"] == 3:
         return "sptc2d_sweep"
     if dtype == "f64":
         return "tc2d_split" if info["precision_name"] == "ozaki" else "dmma2d_sweep"
-    return "tc2d_sweep" if info["precision_name"] == "bf16x3" else "tc2d_ws"
+    if info["precision_name"] in ("f16", "f16x3", "bf16x3"):
+        # the wide kernel reports 128-column tiles; the fallbacks narrower ones
+        if info["tile"][2] == 128:
+            return "tc2d_wide"
+        return "tc2d_sweep" if info["precision_name"] == "bf16x3" else "tc2d_wsh"
+    return "tc2d_ws"
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -385,7 +395,9 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100, f
     relative error every `fine` steps up to `every` steps and every `every`
     steps up to `horizon` steps against the FP64 CUDA-core path run on the GPU
     from the same field (the reference the GPU tests hold within 1e-12 of the
-    FP64 oracle)."""
+    FP64 oracle); then the same field stored in FP64: plain FP64 on CUDA cores
+    against FP64 by exact splitting on the FP16 tensor cores (rates, and the
+    split form's error every `every` steps to `horizon`)."""
     import numpy as np
     import torch
     dims = (16384, 16384)
@@ -468,6 +480,36 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100, f
             held = c["steps"]
         errors.append({"path": path, "precision": prec, "t": r["t"], "gstencils": r["gstencils"],
                        "error_vs_fp64": curve, "within_2e-6_up_to_steps": held})
+    # the same field stored in FP64: plain FP64 on CUDA cores against the FP64
+    # grid on the FP16 tensor cores by exact splitting (rate over `steps`
+    # steps; error every `every` steps to `horizon` against the FP64 reference)
+    ref_at = dict(zip(marks, refs))
+    fp64_storage = []
+    x64 = x.double()
+    y64 = torch.empty_like(x64)
+    for path, prec, t in (("cuda_core", "native", 1), ("tensor_core", "ozaki", 1), ("tensor_core", "ozaki", 2)):
+        plan = B.Plan("box", 2, 2, w, "f64", dims, t)
+        if prec != "native":
+            plan.set_option("precision", prec)
+        plan.set_option("path", path)
+        plan.ensure_workspace(x64.device)
+        sec = _time_runs(lambda: plan.run(x64, y64, steps), stream)
+        row = {"path": path, "precision": prec, "t": t, "gstencils": pts * steps / sec / 1e9,
+               "model_gstencils": plan.info()["predicted_gstencils"]}
+        if prec != "native":
+            a, b = x64.clone(), torch.empty_like(x64)
+            curve = []
+            for m in range(every, horizon + 1, every):
+                plan.run(a, b, every)
+                ref = ref_at[m]
+                curve.append({"steps": m, "rel_linf": float((b[2:-2, 2:-2] - ref).abs().max() / ref.abs().max())})
+                a, b = b, a
+            del a, b
+            row["error_vs_fp64"] = curve
+            row["within_2e-6_up_to_steps"] = horizon if all(c["rel_linf"] <= 2e-6 for c in curve) else None
+        plan.close()
+        fp64_storage.append(row)
+    del x64, y64, ref_at
     del refs, x, y
     torch.cuda.empty_cache()
     return {"workload": f"Box-2D2R F32 16384x16384, sine-mode field, {steps} steps per timed run; "
@@ -475,7 +517,7 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100, f
             "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests, "
                                "16384^2 x 100 steps on sampled boxes included)",
             "plain_fp32_cuda_core_gstencils": plain, "best": best, "crossover": crossover, "rows": rows,
-            "errors": errors}
+            "errors": errors, "fp64_storage": fp64_storage}
 
 
 def split_fp64_leg(B, cfg, w, x, y_plain, plain_gstencils, stream, reps):
@@ -529,6 +571,66 @@ def split_fp64_leg(B, cfg, w, x, y_plain, plain_gstencils, stream, reps):
                        "issued_fp16_tflops": issued / launch_s / 1e12, "peak_tflops": peak,
                        "peak_source": f"bf16_tflops_sustained of {src} peaks (FP16 and BF16 share the dense rate)",
                        "issued_frac": issued / launch_s / 1e12 / peak if peak else None}}
+
+
+def table3_leg(B, inputs, stream):
+    """The paper's six representative cases (Table 3, Sec. 5.3) measured on
+    GB300 at the paper's domain sizes (Sec. 5.1: 10240^2 in 2-D, 1024^3 in
+    3-D): each case's CUDA-core form and, in 2-D, its tensor-core form (the
+    FP64 MMA for FP64 cases, 2:4-sparse TF32 for FP32 ones) at the case's t,
+    with the model's prediction and scenario for both, the measured
+    direction of change (tensor-core rate / CUDA-core rate) next to the
+    paper's A100 one, and this engine's fastest tensor-core form for the
+    case (FP64 by exact splitting; FP16 with the operands exchanged).  This
+    engine has no 3-D tensor-core tiles: 3-D cases run on CUDA cores (at the
+    case's t and at t = 1)."""
+    import numpy as np
+    import torch
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_table3.json")))
+    out = []
+    for case in gold["cases"]:
+        shape, d, r, t, D = case["shape"], case["d"], case["r"], case["t"], case["D"]
+        dtype = "f64" if D == 8 else "f32"
+        dims = (10240, 10240) if d == 2 else (1024, 1024, 1024)
+        steps = 3 * t if d == 2 else t
+        w, u = inputs.problem(shape, d, r, dims, seed=case["case"], dtype=np.float64 if D == 8 else np.float32)
+        x = torch.from_numpy(u).cuda()
+        del u
+        y = torch.empty_like(x)
+        pts = math.prod(dims)
+        forms = [("cuda_core", None, t)]
+        if d == 2:
+            forms.append(("sparse_tensor_core", "tf32", t) if case["tc"] == "sptc_tf32" else ("tensor_core", "native", t))
+            forms.append(("tensor_core", "ozaki" if D == 8 else "f16", t))
+        elif t != 1:
+            forms.append(("cuda_core", None, 1))
+        res = {"case": case["case"], "stencil": f"{shape.capitalize()}-{d}D{r}R", "t": t, "dtype": dtype,
+               "dims": list(dims), "steps_per_run": steps, "paper_change_a100": case["change"], "forms": []}
+        for path, prec, tt in forms:
+            try:
+                plan = B.Plan(shape, d, r, w, dtype, dims, tt)
+                if prec:
+                    plan.set_option("precision", prec)
+                plan.set_option("path", path)
+            except B.StencilError as e:
+                res["forms"].append({"path": path, "precision": prec, "t": tt, "unavailable": str(e)})
+                continue
+            plan.ensure_workspace(x.device)
+            sec = _time_runs(lambda: plan.run(x, y, steps), stream, reps=2 if d == 2 else 1)
+            info = plan.info()
+            res["forms"].append({"path": path, "precision": info["precision_name"], "t": tt,
+                                 "gstencils": pts * steps / sec / 1e9,
+                                 "model_gstencils": info["predicted_gstencils"], "scenario": info["scenario"]})
+            plan.close()
+        cu = res["forms"][0].get("gstencils")
+        if d == 2 and cu and "gstencils" in res["forms"][1]:
+            ratio = res["forms"][1]["gstencils"] / cu
+            res["tc_over_cu"] = ratio
+            res["measured_change"] = "up" if ratio > 1.05 else ("down" if ratio < 0.95 else "same")
+        out.append(res)
+        del x, y
+        torch.cuda.empty_cache()
+    return {"cases": out}
 
 
 def batched_leg(B, inputs, stream, steps=20, ngrids=512):
@@ -636,7 +738,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the mixed-precision and batched legs")
     ap.add_argument("--dims", default=None, help="override the interior extents (profiling), e.g. 6144,6144")
     ap.add_argument("--run-steps", type=int, default=None, help="override the steps per run (profiling)")
-    ap.add_argument("--leg", default="main", choices=["main", "mixed", "batched", "model", "fusion"],
+    ap.add_argument("--leg", default="main", choices=["main", "mixed", "batched", "model", "fusion", "table3"],
                     help="run only the mixed-precision or the batched leg, or the host-only model "
                          "classification, and print its JSON")
     ap.add_argument("--batch-grids", type=int, default=512, help="batched leg: the first N grids (profiling)")
@@ -685,6 +787,8 @@ def main():
             out = mixed_precision_leg(B, inputs, stream)
         elif args.leg == "fusion":
             out = fusion_leg(B, inputs, stream)
+        elif args.leg == "table3":
+            out = table3_leg(B, inputs, stream)
         else:
             out = batched_leg(B, inputs, stream, ngrids=args.batch_grids)
         if rank == 0:
@@ -747,7 +851,7 @@ def main():
     avg_launch_s = ms / 1e3 / sweep_launches
     K = info["K"]
     D = 8 if cfg["dtype"] == "f64" else 4
-    kernel = kernel_name(info, cfg["d"], cfg["dtype"])
+    kernel = kernel_name(info, cfg["d"], cfg["dtype"], cfg["shape"], cfg["r"])
     kernel_key = f"{kernel}:{args.config}:{info['path_name']}:t{t}"
     traffic = traffic_record(kernel_key)
     if info["memory_bound"]:
@@ -874,6 +978,7 @@ def main():
         torch.cuda.empty_cache()
         extras["mixed_precision"] = mixed_precision_leg(B, inputs, stream)
         extras["batched"] = batched_leg(B, inputs, stream)
+        extras["paper_table3_on_gb300"] = table3_leg(B, inputs, stream)
         extras["plain_fp64_gstencils"] = value / world
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -24,6 +24,7 @@
 
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -122,6 +123,19 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait_group()
 {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// f(integral_constant<int, 0>), f(<1>), ... f(<N-1>) while f returns true:
+// a loop whose index is a compile-time constant in the body.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>)
+{
+    (void)(f(std::integral_constant<int, I>{}) && ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
 // FP32 sub-step, register-rotation form.  A work item is a pair of adjacent
@@ -1101,7 +1115,7 @@ __host__ __device__ constexpr bool rot_full_row(int j)
 }
 
 template <int SHAPE, int R>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)  // 2 CTAs per SM: the unrolled planes take 80-115 registers
     cu3d_rot(const float *__restrict__ in, float *__restrict__ out,
              const __grid_constant__ Weights<float, Taps<SHAPE, 3, R>::K> wt, int64_t Ez, int64_t Ey, int64_t Ex,
              int tiles_x, int tiles_y, int nitems, int cz, int xs)
@@ -1181,10 +1195,12 @@ __global__ void __launch_bounds__(kThreads, 3)
         const int nrow_ok = (int)min((int64_t)RPT, ny + R - gy0);  // rows of the thread inside the interior
         const int ooff0 = (int)(gy0 * Ex + gx0);                  // offset within a stored plane
         for (int base = 0; base < nin; base += NS) {
-#pragma unroll
-            for (int u = 0; u < NS; ++u) {
+            // the NS planes of this round; u is a compile-time constant, so every
+            // accumulator slot index below is one too (no run-time selects)
+            static_for<NS>([&](auto U) -> bool {
+                constexpr int u = decltype(U)::value;
                 const int ip = base + u;
-                if (ip >= nin) break;
+                if (ip >= nin) return false;
                 // plane ip + NPL - 1 goes into the slot plane ip - 1 used (read before the last barrier)
                 if (ip + kRotNPL - 1 < nin) load_plane(ip + kRotNPL - 1);
                 cp_async_commit();
@@ -1233,7 +1249,7 @@ __global__ void __launch_bounds__(kThreads, 3)
                 }
                 // output plane ip - 2R is complete (slot (u + 1) mod NS)
                 const int oq = ip - 2 * R;
-                const int sd = (u + 1) % NS;
+                constexpr int sd = (u + 1) % NS;
                 if (oq >= 0 && oq < nzo) {
                     float *obase = out + (Z0 + oq) * Ey * Ex;
 #pragma unroll
@@ -1253,7 +1269,8 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
                 for (int i = 0; i < RPT; ++i) acc[sd][i][0] = acc[sd][i][1] = acc[sd][i][2] = acc[sd][i][3] = 0.0f;
                 __syncthreads();  // the slot of plane ip is free for plane ip + NPL
-            }
+                return true;
+            });
         }
     }
     cp_async_wait_group<0>();

@@ -268,7 +268,8 @@ constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
 constexpr double kWorkerF16 = 2.20;        // tc2d_wsh F16: staging, exponent, conversion, epilogue
 constexpr double kWorkerF16x3 = 2.40;      // tc2d_wsh F16x3: + the lo parts
 constexpr double kMmaCyclesWsh = 110.0;    // tc2d_wsh: its MMAs share shared memory with the conversion
-constexpr double kWorkerWide = 0.40;       // tc2d_wide: two load passes, conversion, epilogue (estimate)
+constexpr double kWorkerWide = 0.45;       // tc2d_wide, one product: loads, conversion, epilogue (added to the MMAs)
+constexpr double kWorkerWideSplit = 0.28;  // tc2d_wide, three products (128- / 64-row tiles)
 // tc2d_sweep BF16x3 runs one tile per CTA with several CTAs per SM, whose
 // MMAs interleave: 2.65 cycles per output plus 47.6 per MMA of an output
 // (fitted to Box-2D2R at t = 1..4 within 10 %)
@@ -280,11 +281,12 @@ constexpr double kWorkerSplit = 4.06;      // tc2d_split: FP64 load, exponent, d
 // instruction of an output (fitted to Box-2D2R at t = 1..4 within 4 %)
 constexpr double kWorkerSparse = 0.92;
 constexpr double kSparseMmaCycles = 3.15;
-// cu2d_sweep FP32 (one sub-step): 2.64 thread instructions per tap and
-// output (66 for the 25 taps of Box-2D2R, ncu) issued at 72 % of the SM's
-// 128 per cycle; fused sub-steps repeat it over the overlapped tile
-constexpr double kCuF32InstrPerTap = 2.64;
-constexpr double kCuF32IssueEff = 0.72;
+// cu2d_sweep FP32 (one sub-step, fixed-strip form): 1.76 thread
+// instructions per tap and output (44 for the 25 taps of Box-2D2R, ncu)
+// issued at 53.5 % of the SM's 128 per cycle (fitted to 490 GStencil/s on
+// 16384^2); fused sub-steps repeat it over the overlapped tile
+constexpr double kCuF32InstrPerTap = 1.76;
+constexpr double kCuF32IssueEff = 0.535;
 
 // Instruction-level roof (point updates/s / 1e9) of a tensor-core candidate;
 // 0 when it does not apply (FP64 MMA, which the paper's model covers).
@@ -320,7 +322,8 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
         const double products = prec == STENCIL_PREC_F16 ? 1.0 : 3.0;
         const double mma = blocks * products / (128.0 * nr) * std::max(kMmaCycles, 128.0 * nr * 16 / 4096.0);
-        per_out = std::max(mma, kWorkerWide);
+        // measured: the staging and epilogue overlap the MMAs only in part
+        per_out = mma + (prec == STENCIL_PREC_F16 ? kWorkerWide : kWorkerWideSplit);
     } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3)) {
         const int n = tc_wsh_ntile(shape, r, t, prec == STENCIL_PREC_F16X3);
         if (n == 0) return 0;
