@@ -512,6 +512,20 @@ __device__ __forceinline__ void f32_fixed_dispatch(int D, bool s4, const float *
 #undef GBS_FIXED
 }
 
+// f32_substep4_fixed with strips of 2 rows (radii 3 and more).
+template <int SHAPE, int R, typename WT>
+__device__ __forceinline__ void f32_fixed_dispatch2(int D, const float *__restrict__ src, float *__restrict__ dst,
+                                                    float *__restrict__ out, const WT &wt, int P, int lo, int hiY,
+                                                    int hiX, int64_t Y0, int64_t X0, int64_t Ex, bool last)
+{
+    switch (D) {
+    case 0: f32_substep4_fixed<SHAPE, R, 0, 2>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex, last); break;
+    case 1: f32_substep4_fixed<SHAPE, R, 1, 2>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex, last); break;
+    case 2: f32_substep4_fixed<SHAPE, R, 2, 2>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex, last); break;
+    default: f32_substep4_fixed<SHAPE, R, 3, 2>(src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex, last); break;
+    }
+}
+
 // Persistent form: CTA b processes tiles b, b + gridDim.x, ...; while it
 // computes one tile it prefetches the next into the other staging buffer
 // with cp.async, so the FMA pipe never waits for a synchronous load phase.
@@ -615,12 +629,25 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && R <= 3) ? 3 : 2)
             const bool last = s == t;
             if constexpr (sizeof(T) == 4) {
                 const bool all_int = Y0 + lo >= R && Y0 + hiY <= Ey - R && X0 + lo >= R && X0 + hiX <= Ex - R;
-                if constexpr (R <= 2) {  // R = 3 would spill next to the rotation form
+                if constexpr (R <= 2) {
                     if (all_int && ring.band == 0 && (cw & 3) == 0 && ch >= 8) {
                         // strips of 8 rows, or of 4 when that tiles the region exactly
                         const bool s4 = (ch & 7) != 0 && (ch & 3) == 0;
                         f32_fixed_dispatch<SHAPE, R>((lo - R) & 3, s4, src, dst, out, wt, P, lo, hiY, hiX, Y0, X0,
                                                      Ex, last);
+                        __syncthreads();
+                        T *tmp = src;
+                        src = dst;
+                        dst = tmp;
+                        continue;
+                    }
+                } else {
+                    // larger radii: strips of 2 rows (each item reads 2 + 2R rows
+                    // for 8 outputs: loads stay a few % of the (2R+1)^2 taps, and
+                    // the unrolled code stays a few thousand FMAs)
+                    if (all_int && ring.band == 0 && (cw & 3) == 0 && ch >= 2) {
+                        f32_fixed_dispatch2<SHAPE, R>((lo - R) & 3, src, dst, out, wt, P, lo, hiY, hiX, Y0, X0, Ex,
+                                                      last);
                         __syncthreads();
                         T *tmp = src;
                         src = dst;

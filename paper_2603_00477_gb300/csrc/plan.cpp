@@ -281,12 +281,14 @@ constexpr double kWorkerSplit = 4.06;      // tc2d_split: FP64 load, exponent, d
 // instruction of an output (fitted to Box-2D2R at t = 1..4 within 4 %)
 constexpr double kWorkerSparse = 0.92;
 constexpr double kSparseMmaCycles = 3.15;
-// cu2d_sweep FP32 (one sub-step, fixed-strip form): 1.76 thread
-// instructions per tap and output (44 for the 25 taps of Box-2D2R, ncu)
-// issued at 53.5 % of the SM's 128 per cycle (fitted to 490 GStencil/s on
-// 16384^2); fused sub-steps repeat it over the overlapped tile
-constexpr double kCuF32InstrPerTap = 1.76;
+// cu2d_sweep FP32 (one sub-step, fixed-strip form): one FMA per tap plus
+// ~19 other thread instructions per output (44 for the 25 taps of Box-2D2R,
+// ncu), issued at 53.5 % of the SM's 128 per cycle; fused sub-steps repeat it
+// over the overlapped tile.  Its one-step sweep saturates at ~58 % of the
+// HBM roof (490 / 457 GStencil/s for Box- / Star-2D2R on 16384^2).
+constexpr double kCuF32InstrPerOut = 19.0;
 constexpr double kCuF32IssueEff = 0.535;
+constexpr double kCuF32HbmEff = 0.58;
 
 // Instruction-level roof (point updates/s / 1e9) of a tensor-core candidate;
 // 0 when it does not apply (FP64 MMA, which the paper's model covers).
@@ -364,8 +366,9 @@ static double cu_gstencils(const Plan &p, int t, const int tile[3])
     const double ovl = cu_overlap_factor(p, t, tile);
     double g = std::min(P_cu / (2.0 * K) / ovl, t * pk.hbm_bytes_per_s / (2.0 * D)) / 1e9;
     if (p.dtype == STENCIL_F32 && p.pat.d == 2) {
-        const double per_out = ovl * t * K * kCuF32InstrPerTap / (128.0 * kCuF32IssueEff);
+        const double per_out = ovl * t * (K + kCuF32InstrPerOut) / (128.0 * kCuF32IssueEff);
         g = std::min(g, t * (pk.cu_f32_flops / 256.0) / per_out / 1e9);
+        g = std::min(g, t * kCuF32HbmEff * pk.hbm_bytes_per_s / (2.0 * D) / 1e9);
     }
     return g;
 }

@@ -258,12 +258,12 @@ def test_dispatch_fp32_paper_model_and_issue_roof(lib):
     """Box-2D2R FP32 on CUDA cores.  The paper's model (Eq. 8, no instruction
     costs) classifies it memory-bound at t = 1 (I = 6.25 against a ridge of
     80.5 TFLOP/s / 6.8 TB/s = 11.8) and compute-bound from t = 2.  The
-    FP32 sub-step this library runs is issue-bound instead (1.76 instructions
-    per tap and output at 53.5 % issue): its issue roof,
-    t * 152 * 2.07e9 / (overlap * t * 25 * 1.76 / (128 * 0.535)), is below the
-    HBM roof 6.8e12 / 8 = 850 G at every t and falls with t through the
-    overlap, so the dispatcher keeps t = 1 (measured on GB300: 490 at t = 1,
-    489 at t = 2 GStencil/s)."""
+    FP32 sub-step this library runs is issue-bound instead (25 FMAs and ~19
+    other instructions per output at 53.5 % issue): its issue roof,
+    t * 152 * 2.07e9 / (overlap * t * (25 + 19) / (128 * 0.535)), is below
+    58 % of the HBM roof 6.8e12 / 8 = 850 G (where the one-step sweep
+    saturates) and falls with t through the overlap, so the dispatcher keeps
+    t = 1 (measured on GB300: 490 at t = 1, 488 at t = 2 GStencil/s)."""
     pk = B.stencil_get_peaks()
     m1 = B.stencil_model_predict("box", 2, 2, 1, 4, 1.0, 1.0, pk["cu_f32_flops"], pk["cu_f32_flops"],
                                  pk["hbm_bytes_per_s"])
@@ -274,7 +274,8 @@ def test_dispatch_fp32_paper_model_and_issue_roof(lib):
     try:
         info = B.stencil_plan_info(p)
         assert info["path"] == B.PATH_CUDA_CORE and info["t"] == 1
-        issue_roof = 152 * 2.07e9 / (25 * 1.76 / (128 * 0.535)) / 1e9
+        issue_roof = 152 * 2.07e9 / ((25 + 19) / (128 * 0.535)) / 1e9
+        assert issue_roof < 0.58 * pk["hbm_bytes_per_s"] / 8 / 1e9
         assert info["predicted_gstencils"] == pytest.approx(issue_roof, rel=1e-6)
         assert info["predicted_gstencils"] < pk["hbm_bytes_per_s"] / 8 / 1e9
     finally:

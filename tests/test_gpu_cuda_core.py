@@ -80,6 +80,12 @@ CASES_2D = [
     ("box", 2, (200, 600), 5, 2, "f32", None),
     ("box", 2, (170, 530), 3, 3, "f32", "42x128"),     # strips overlap (ch not a multiple of 4)
     ("box", 1, (99, 1030), 2, 1, "f32", None),
+    # FP32, r >= 3: strips of 2 rows on whole interior tiles (64 x 128)
+    ("box", 3, (300, 530), 3, 1, "f32", None),
+    ("box", 7, (200, 300), 2, 1, "f32", None),
+    ("star", 5, (260, 400), 3, 2, "f32", None),
+    ("box", 4, (300, 301), 2, 2, "f32", None),          # unaligned rows
+    ("star", 7, (150, 390), 2, 1, "f32", None),
 ]
 
 
