@@ -432,6 +432,16 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100, f
         crossover.append({"t": t, "model_winner": m["path"], "measured_winner": g["path"],
                           "cuda_core_gstencils": next(r["gstencils"] for r in at if r["path"] == "cuda_core"),
                           "best_tensor_gstencils": max(r["gstencils"] for r in at if r["path"] != "cuda_core")})
+    # the same over every form (FP16 has TF32's normwise error; the 3-product
+    # forms are more accurate)
+    crossover_all = []
+    for t in (1, 2, 3, 4):
+        at = [r for r in rows if r["t"] == t]
+        m = max(at, key=lambda r: r["model_gstencils"])
+        g = max(at, key=lambda r: r["gstencils"])
+        crossover_all.append({"t": t, "model_winner": f'{m["path"]}:{m["precision"]}',
+                              "measured_winner": f'{g["path"]}:{g["precision"]}',
+                              "measured_best_gstencils": g["gstencils"]})
 
     # error growth: FP64 reference states every `fine` steps to `every`, then
     # every `every` steps (kept on the GPU)
@@ -516,7 +526,8 @@ def mixed_precision_leg(B, inputs, stream, steps=100, horizon=1000, every=100, f
                         f"error every {every} steps to {horizon}",
             "error_reference": "FP64 CUDA-core path on the GPU (held within 1e-12 of the FP64 oracle by the GPU tests, "
                                "16384^2 x 100 steps on sampled boxes included)",
-            "plain_fp32_cuda_core_gstencils": plain, "best": best, "crossover": crossover, "rows": rows,
+            "plain_fp32_cuda_core_gstencils": plain, "best": best, "crossover": crossover,
+            "crossover_all_forms": crossover_all, "rows": rows,
             "errors": errors, "fp64_storage": fp64_storage}
 
 
@@ -871,6 +882,9 @@ def main():
         probe = B.stencil_probe_peaks(stream)
         measured = probe["cu_f64_flops" if D == 8 else "cu_f32_flops"] / 1e12
         roof["probe_peak"] = measured
+        roof["probe_peak_source"] = ("stencil_probe_peaks: register-only FMA chains on every SM at the maximum "
+                                     "clock; for FP64 they reach ~3.2 of the 4 FLOP per SM cycle that this "
+                                     "sweep sustains, so the peak above is the derived one")
         roof["probe_frac"] = roof["achieved"] / measured
     roof["traffic"] = traffic
     roof["kernel"] = kernel_key

@@ -478,9 +478,14 @@ stencil_status stencil_set_peaks(const stencil_peaks *peaks);
 stencil_status stencil_get_peaks(stencil_peaks *peaks);
 
 /* Measure the FP64 and FP32 FMA-pipe rates of the current device (FLOP/s,
- * independent FMA chains in registers, timed with CUDA events on `stream`;
- * synchronises `stream`).  Fills cu_f64_flops and cu_f32_flops, zeroes the
- * other fields; does not change the dispatcher's table.  Takes about a
+ * independent FMA chains in registers on every SM, one launch each on
+ * `stream`; synchronises `stream`): the launch's FLOP per second (CUDA
+ * events) scaled from the SM clock it ran at (clock64 against the global
+ * timer) to the device's maximum SM clock.  On GB300 the FP64 figure
+ * (~1.01-1.06 TFLOP/s) is below the 1.24 TFLOP/s that the FP64 stencil sweep
+ * itself sustains: register-only FMA chains do not reach the FP64 pipe's
+ * 4 FLOP per SM cycle.  Fills cu_f64_flops and cu_f32_flops, zeroes
+ * the other fields; does not change the dispatcher's table.  Takes about a
  * second. */
 stencil_status stencil_probe_peaks(stencil_peaks *measured, stencil_stream_t stream);
 

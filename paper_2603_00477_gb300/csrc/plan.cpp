@@ -20,6 +20,8 @@
 #include <stdexcept>
 #include <string>
 
+#include <cuda_runtime.h>
+
 #include "internal.h"
 #include "tc_layout.h"
 
@@ -79,6 +81,18 @@ static int max_fused_t(const Plan &p, int path)
     return 4;
 }
 
+// SMs of the current device (152 when no device answers: host-only use).
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();  // clear the error of a host without a device
+        return 152;
+    }
+    return sms;
+}
+
 void cu_default_tile(const Plan &p, int t, int tile[3])
 {
     const int R = p.pat.r;
@@ -99,6 +113,17 @@ void cu_default_tile(const Plan &p, int t, int tile[3])
             size_t bytes = h * w * p.elem_bytes() * (t > 1 ? 3 : 2);
             if (bytes <= 112 * 1024 || (tile[2] <= 16 && tile[1] <= 16)) break;
             if (tile[2] >= tile[1]) tile[2] /= 2; else tile[1] /= 2;
+        }
+        // small grids: at least two tiles per SM (down to 16 x 32 tiles), so
+        // that a sweep of a few hundred thousand points is not a few CTAs' work
+        const int64_t want = 2 * (int64_t)device_sms();
+        auto ntiles = [&] {
+            return ((p.dims[1] + tile[1] - 1) / tile[1]) * ((p.dims[2] + tile[2] - 1) / tile[2]);
+        };
+        while (ntiles() < want) {
+            if (tile[2] >= tile[1] && tile[2] > 32) tile[2] /= 2;
+            else if (tile[1] > 16) tile[1] /= 2;
+            else break;
         }
     } else if (t == 1) {
         // the streaming kernels: runs of planes (64 nominal; the rotating
