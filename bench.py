@@ -244,10 +244,7 @@ def kernel_name(info: dict, d: int, dtype: str, shape: str = "box", r: int = 1) 
     if dtype == "f64":
         return "tc2d_split" if info["precision_name"] == "ozaki" else "dmma2d_sweep"
     if info["precision_name"] in ("f16", "f16x3", "bf16x3"):
-        # the wide kernel reports 128-column tiles; the fallbacks narrower ones
-        if info["tile"][2] == 128:
-            return "tc2d_wide"
-        return "tc2d_sweep" if info["precision_name"] == "bf16x3" else "tc2d_wsh"
+        return "tc2d_wide"
     return "tc2d_ws"
 
 

@@ -14,13 +14,11 @@
 //   tc2d_ws (TF32, TF32X3): warp-specialised persistent kernel, TN = 32 (or
 //     16 / 8 where the operands would not fit), double-buffered operands and
 //     accumulators (below).
-//   tc2d_sweep (BF16X3, kind::f16): one tile per CTA, TN = 8; one thread
-//     issues all MMAs of the tile and commits them to an mbarrier, the four
-//     warps read the accumulators back with tcgen05.ld and store rows.
 //
-// Precision forms: TF32 (one product of TF32-rounded operands), TF32X3 and
-// BF16X3 (each operand split into hi + lo, three products hi*hi + hi*lo +
-// lo*hi accumulated in FP32).
+// Precision forms here: TF32 (one product of TF32-rounded operands) and
+// TF32X3 (each operand split into hi + lo, three products hi*hi + hi*lo +
+// lo*hi accumulated in FP32).  The FP16 / BF16 forms run on the wide kernel
+// (k_wide.cu), which exchanges the roles of the two operands.
 //
 // FP64 grids (dmma2d_sweep): the same Toeplitz formulation on the FP64 MMA
 // mma.sync.m8n8k4 (M = 8 output rows, N = 8 output columns, K = 4).
@@ -29,8 +27,6 @@
 // nearer points would need the halo re-imposed between the fused steps; the
 // CUDA-core band kernel computes them stepwise.
 #include <cuda.h>
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -58,7 +54,6 @@ struct TcParams {
     int vec16;        // tc2d_ws: stage 16-byte chunks (stored rows are 16-byte multiples)
     int xshift;       // tc2d_ws: tiles start xshift columns left of column 0 (aligned windows)
     int tma;          // tc2d_ws: stage tiles with TMA (one box per 16-byte chunk column)
-    int ew;           // tc2d_wsh: the composite weights are scaled by 2^-ew (|w| 2^-ew < 1)
     int64_t Ey, Ex;
 };
 
@@ -70,50 +65,13 @@ using namespace tc;
 
 constexpr int TM = 128;
 constexpr int TN = 8;
-enum { P_TF32 = 0, P_TF32X3 = 1, P_BF16X3 = 2 };
-
-template <int PREC>
-struct Elem;
-template <>
-struct Elem<P_TF32> {
-    static constexpr int bytes = 4;
-};
-template <>
-struct Elem<P_TF32X3> {
-    static constexpr int bytes = 4;
-};
-template <>
-struct Elem<P_BF16X3> {
-    static constexpr int bytes = 2;
-};
-
-template <int PREC>
-__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, float v)
-{
-    if (PREC == P_BF16X3) {
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
-        *reinterpret_cast<__nv_bfloat16 *>(hi) = h;
-        *reinterpret_cast<__nv_bfloat16 *>(lo) = l;
-    } else if (PREC == P_TF32X3) {
-        float h = to_tf32(v);
-        *reinterpret_cast<float *>(hi) = h;
-        *reinterpret_cast<float *>(lo) = to_tf32(v - h);
-    } else {
-        *reinterpret_cast<float *>(hi) = to_tf32(v);
-    }
-}
+enum { P_TF32 = 0, P_TF32X3 = 1 };
 
 // hi/lo split of a weight given in FP64: hi = round(w), lo = round(w - hi).
 template <int PREC>
 __device__ __forceinline__ void split_store_w(unsigned char *hi, unsigned char *lo, double w)
 {
-    if (PREC == P_BF16X3) {
-        __nv_bfloat16 h = __float2bfloat16_rn((float)w);
-        __nv_bfloat16 l = __float2bfloat16_rn((float)(w - (double)__bfloat162float(h)));
-        *reinterpret_cast<__nv_bfloat16 *>(hi) = h;
-        *reinterpret_cast<__nv_bfloat16 *>(lo) = l;
-    } else if (PREC == P_TF32X3) {
+    if (PREC == P_TF32X3) {
         float h = to_tf32((float)w);
         *reinterpret_cast<float *>(hi) = h;
         *reinterpret_cast<float *>(lo) = to_tf32((float)(w - (double)h));
@@ -138,157 +96,6 @@ __device__ __forceinline__ bool wait_mbar_cycles(uint64_t *mbar, uint32_t phase,
         if (clock64() - t0 > limit) return false;
     }
     return true;
-}
-
-template <int PREC, int NACC>
-__global__ void __launch_bounds__(128) tc2d_sweep(const float *__restrict__ in, float *__restrict__ out,
-                                                  const __grid_constant__ TcParams p)
-{
-    constexpr bool SPLIT = PREC != P_TF32;
-    constexpr int ES = Elem<PREC>::bytes;
-    constexpr int E = 16 / ES;  // elements per 16-byte chunk
-    constexpr int KI = 2 * E;   // MMA K per instruction (32 bytes of K)
-    constexpr int TX = NACC * TN;
-    constexpr int SP = TX + 4;  // staging row pitch (floats)
-    // split forms keep two accumulators per output tile: the hi*hi products and
-    // the small hi*lo + lo*hi corrections, added in FP32 in the epilogue, so the
-    // corrections are not rounded at the magnitude of the main sum
-    constexpr uint32_t kCols = NACC * TN * (SPLIT ? 2 : 1);
-    constexpr uint32_t kCorr = NACC * TN;  // column offset of the correction accumulators
-    static_assert(kCols >= 32 && (kCols & (kCols - 1)) == 0, "TMEM columns: power of two >= 32");
-
-    extern __shared__ __align__(1024) unsigned char smem[];
-    const int R = p.R, HS = p.hs, NCH = p.nch, nkb = p.nkb;
-    const int lines = 2 * R + 1;
-    const uint32_t a_bytes = (uint32_t)NCH * HS * 16;
-    const uint32_t b_bytes = (uint32_t)lines * nkb * 256;
-    // [0,16): TMEM address + mbarrier; operands from byte 128
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + 8);
-    unsigned char *A0 = smem + 128;
-    unsigned char *A1 = A0 + (SPLIT ? a_bytes : 0);
-    unsigned char *B0 = A0 + a_bytes * (SPLIT ? 2 : 1);
-    unsigned char *B1 = B0 + (SPLIT ? b_bytes : 0);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t Y0 = p.rh + (int64_t)blockIdx.y * TM;  // stored row of output row 0
-    const int64_t X0 = p.rh + (int64_t)blockIdx.x * TX;  // stored column of output column 0
-    const int64_t ny = p.Ey - 2 * p.rh, nx = p.Ex - 2 * p.rh;
-
-    if (warp == 0) tmem_alloc(tmem_slot, kCols);
-    if (tid == 0) {
-        mbar_init(mbar, 1);
-        fence_mbar_init();
-    }
-
-    // Toeplitz blocks: block (line a, k-block kb) holds B_a[kb*KI + k][n] for
-    // n < 8, k < KI as two core matrices (k chunks) of 8 rows (n) x 16 bytes.
-    const int bent = lines * nkb * 8 * KI;
-    for (int idx = tid; idx < bent; idx += blockDim.x) {
-        const int k = idx % KI;
-        const int n = (idx / KI) % 8;
-        const int blk = idx / (8 * KI);  // = ai * nkb + kb
-        const int ai = blk / nkb, kb = blk % nkb;
-        const int b = kb * KI + k - n - R;
-        const double wv = (b >= -R && b <= R) ? p.w[ai * lines + (b + R)] : 0.0;
-        const uint32_t off = blk * 256 + (k / E) * 128 + n * 16 + (k % E) * ES;
-        split_store_w<PREC>(B0 + off, B1 + off, wv);
-    }
-    // Input tile: rows Y0-R .. Y0+TM+R-1, columns X0-R .. X0-R+NCH*E-1.
-    const int rows = TM + 2 * R, cols = NCH * E;
-    for (int row = warp; row < rows; row += 4) {
-        const int64_t gy = Y0 - R + row;
-        const bool rowok = gy >= 0 && gy < p.Ey;
-        const float *src = in + gy * p.Ex;
-        for (int x = lane; x < cols; x += 32) {
-            const int64_t gx = X0 - R + x;
-            const float v = (rowok && gx >= 0 && gx < p.Ex) ? __ldg(src + gx) : 0.0f;
-            const uint32_t off = (uint32_t)(x / E) * HS * 16 + row * 16 + (x % E) * ES;
-            split_store<PREC>(A0 + off, A1 + off, v);
-        }
-    }
-    fence_proxy_async_smem();
-    fence_before_thread_sync();
-    __syncthreads();
-    fence_after_thread_sync();
-    const uint32_t tmem = *tmem_slot;
-
-    if (tid == 0) {
-        const uint32_t idesc = instr_desc(PREC == P_BF16X3 ? kFmtBF16 : kFmtTF32, TM, TN);
-        const uint32_t a0 = smem_u32(A0), a1 = smem_u32(A1), b0 = smem_u32(B0), b1 = smem_u32(B1);
-        const uint32_t lbo_a = (uint32_t)HS * 16;
-        // q innermost: consecutive MMAs go to different accumulators
-        uint32_t acc = 0;
-        for (int ai = 0; ai < lines; ++ai) {
-            for (int kb = p.kb_lo[ai]; kb <= p.kb_hi[ai]; ++kb) {
-                for (int q = 0; q < NACC; ++q) {
-                    const uint32_t d = tmem + q * TN;
-                    const uint32_t dc = d + kCorr;
-                    const uint32_t aoff = (uint32_t)(q * (TN / E) + 2 * kb) * lbo_a + ai * 16;
-                    const uint32_t boff = (uint32_t)(ai * nkb + kb) * 256;
-                    const uint64_t da0 = smem_desc(a0 + aoff, lbo_a, 128);
-                    const uint64_t db0 = smem_desc(b0 + boff, 128, 256);
-                    if (PREC == P_BF16X3) {
-                        mma_f16(d, da0, db0, idesc, acc);
-                        mma_f16(dc, da0, smem_desc(b1 + boff, 128, 256), idesc, acc);
-                        mma_f16(dc, smem_desc(a1 + aoff, lbo_a, 128), db0, idesc, 1);
-                    } else {
-                        mma_tf32(d, da0, db0, idesc, acc);
-                        if (SPLIT) {
-                            mma_tf32(dc, da0, smem_desc(b1 + boff, 128, 256), idesc, acc);
-                            mma_tf32(dc, smem_desc(a1 + aoff, lbo_a, 128), db0, idesc, 1);
-                        }
-                    }
-                }
-                acc = 1;  // every accumulator has had its first (overwriting) MMA
-            }
-        }
-        mma_commit(mbar);
-    }
-    __syncwarp();
-    const bool done = wait_mbar_cycles(mbar, 0);
-    bool ok = done;
-    // test hook: once phase 0 has completed the barrier sits in phase 1, which
-    // no arrival will ever complete, so this wait runs out
-    if (p.debug_unmet && done) ok = wait_mbar_cycles(mbar, 1, kDebugWaitCycles);
-    fence_after_thread_sync();
-    if (!ok) {
-        atomicExch(&g_tc_error, 1);
-        if (!done) wait_mbar_cycles(mbar, 0);  // give in-flight MMAs a second chance before freeing TMEM
-    }
-    __syncthreads();  // every thread has seen the MMAs complete before the operands are reused
-    if (ok) {
-        // TMEM -> registers -> staging (reuses the operand area: the MMAs are done)
-        float *stage = reinterpret_cast<float *>(A0);
-        const int m = warp * 32 + lane;
-        for (int q = 0; q < NACC; ++q) {
-            uint32_t v[8], c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-            tmem_ld_32x32b_x8(lane_base + q * TN, v);
-            if (SPLIT) tmem_ld_32x32b_x8(lane_base + kCorr + q * TN, c);
-            tmem_ld_wait();
-            float f[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) f[j] = __uint_as_float(v[j]) + (SPLIT ? __uint_as_float(c[j]) : 0.0f);
-            float4 *dst = reinterpret_cast<float4 *>(stage + m * SP + q * TN);
-            dst[0] = make_float4(f[0], f[1], f[2], f[3]);
-            dst[1] = make_float4(f[4], f[5], f[6], f[7]);
-        }
-        __syncthreads();
-        for (int row = warp; row < TM; row += 4) {
-            const int64_t gy = Y0 + row;
-            const int64_t iy = gy - p.rh;
-            if (iy >= ny) break;
-            float *dstrow = out + gy * p.Ex;
-            for (int x = lane; x < TX; x += 32) {
-                const int64_t ix = X0 + x - p.rh;
-                if (ix < nx && outside_band(iy, ix, ny, nx, p.band)) dstrow[X0 + x] = stage[row * SP + x];
-            }
-        }
-    }
-    fence_before_thread_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,352 +482,6 @@ __global__ void __launch_bounds__(256) dmma2d_sweep(const double *__restrict__ i
     }
 }
 
-// ---------------------------------------------------------------------------
-// Warp-specialised FP16 sweep with per-tile power-of-two scaling (precision
-// F16: one product; F16X3: hi + lo parts, three products), persistent CTAs,
-// 288 threads.
-//
-// A tcgen05.mma kind::f16 takes 16 values of K per instruction, twice the
-// TF32 kind's 8, for the same fixed per-instruction cost, so the same
-// Toeplitz tile needs half the MMAs.  FP16's 11-bit significand equals
-// TF32's; its range is covered by scaling: every staged tile is multiplied
-// by 2^-eu (eu: its largest exponent, so the scaled values lie in (-1, 1)),
-// the composite weights by 2^-ew, and the accumulators by 2^(eu + ew) in the
-// epilogue (exact power-of-two multiplications).  Values below 2^-24 of the
-// tile's largest become FP16 subnormals or zero, far below the 2^-11
-// rounding of the normwise error.
-//
-// Warps 0-7: cp.async of tile k+1 (FP32, chunk-column layout, 4 values per
-// 16-byte chunk, double-buffered) while tile k is converted; each thread then
-// reduces the exponent of the chunks it copied itself, the workers exchange
-// their maxima through an mbarrier (bounded wait), and convert the FP32 tile
-// into the FP16 operand layout (8 values per chunk; hi, and lo = x - hi for
-// F16X3, double-buffered); warps 0-3 drain the previous tile's accumulators.
-// Warp 8 issues the MMAs exactly like tc2d_ws.
-// ---------------------------------------------------------------------------
-enum { P_F16 = 3, P_F16X3 = 4 };
-
-__device__ __forceinline__ float pow2f(int e)  // 2^e for -126 <= e <= 127
-{
-    return __int_as_float((e + 127) << 23);
-}
-
-template <int PREC, int TN_, int NACC>
-__global__ void __launch_bounds__(288, 1)
-    tc2d_wsh(const float *__restrict__ in, float *__restrict__ out, const __grid_constant__ TcParams p, int ntiles,
-             int ntx)
-{
-    constexpr bool SPLIT = PREC == P_F16X3;
-    constexpr int TX = NACC * TN_;
-    constexpr uint32_t kSet = NACC * TN_ * (SPLIT ? 2 : 1);
-    constexpr uint32_t kCols = 2 * kSet <= 32 ? 32 : (2 * kSet <= 64 ? 64 : (2 * kSet <= 128 ? 128 : (2 * kSet <= 256 ? 256 : 512)));
-    constexpr uint32_t kCorr = NACC * TN_;
-    constexpr uint32_t kBlk = (TN_ / 8) * 256;  // one Toeplitz block: TN rows x 16 k (two 8-value chunks)
-    static_assert(2 * kSet <= 512, "TMEM columns");
-
-    extern __shared__ __align__(1024) unsigned char smem[];
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem);
-    int *abort_flag = reinterpret_cast<int *>(smem + 4);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 16);   // [2]
-    uint64_t *done = reinterpret_cast<uint64_t *>(smem + 32);   // [2]
-    uint64_t *freeb = reinterpret_cast<uint64_t *>(smem + 48);  // [2]
-    uint64_t *maxb = reinterpret_cast<uint64_t *>(smem + 64);   // [2]: staged tile and its exponent
-    int *wmax = reinterpret_cast<int *>(smem + 80);             // [2][8], bytes 80..143
-    const int R = p.R, HS = p.hs, NCH = p.nch;                  // NCH: 8-value chunks of the window
-    const int lines = 2 * R + 1, nkb = p.nkb;
-    const uint32_t raw_bytes = (uint32_t)(2 * NCH) * HS * 16;   // FP32 staging (4-value chunks)
-    const uint32_t a_bytes = (uint32_t)NCH * HS * 16;           // one FP16 operand buffer
-    const uint32_t b_bytes = (uint32_t)lines * nkb * kBlk;
-    unsigned char *B0 = smem + 256;
-    unsigned char *B1 = B0 + (SPLIT ? b_bytes : 0);
-    unsigned char *raw0 = B0 + b_bytes * (SPLIT ? 2 : 1);
-    float *raw[2] = {reinterpret_cast<float *>(raw0), reinterpret_cast<float *>(raw0 + raw_bytes)};
-    unsigned char *abase = raw0 + 2 * raw_bytes;
-    unsigned char *Ahi[2] = {abase, abase + a_bytes};
-    unsigned char *Alo[2] = {abase + 2 * a_bytes, abase + 3 * a_bytes};
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t Ey = p.Ey, Ex = p.Ex, rh = p.rh;
-    const int64_t ny = Ey - 2 * rh, nx = Ex - 2 * rh;
-
-    if (warp == 0) tmem_alloc(tmem_slot, kCols);
-    if (tid == 0) {
-        *abort_flag = 0;
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&full[b], 256);
-            mbar_init(&done[b], 1);
-            mbar_init(&freeb[b], 128);
-            mbar_init(&maxb[b], 256);
-        }
-        fence_mbar_init();
-    }
-    // Toeplitz blocks of the scaled weights: block (line, kb) = TN rows (n) x
-    // 16 k, K-major core matrices (n-group i, k-chunk j) at i*256 + j*128
-    const float wsc = pow2f(-p.ew);
-    const int bent = lines * nkb * TN_ * 16;
-    for (int idx = tid; idx < bent; idx += blockDim.x) {
-        const int k = idx % 16, n = (idx / 16) % TN_, blk = idx / (16 * TN_);
-        const int ai = blk / nkb, kb = blk % nkb;
-        const int b = kb * 16 + k - n - R;
-        const double wv = (b >= -R && b <= R) ? p.w[ai * lines + (b + R)] : 0.0;
-        const uint32_t off = blk * kBlk + (n / 8) * 256 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
-        const double wsd = wv * (double)wsc;  // exact: a power-of-two scaling
-        const __half h = __float2half_rn((float)wsd);
-        *reinterpret_cast<__half *>(B0 + off) = h;
-        if (SPLIT) *reinterpret_cast<__half *>(B1 + off) = __float2half_rn((float)(wsd - (double)__half2float(h)));
-    }
-    fence_proxy_async_smem();
-    fence_before_thread_sync();
-    __syncthreads();
-    fence_after_thread_sync();
-    const uint32_t tmem = *tmem_slot;
-
-    auto bounded_wait = [&](uint64_t *bar, uint32_t parity, unsigned long long limit) -> bool {
-        const unsigned long long t0 = clock64();
-        while (!mbar_try_wait(bar, parity)) {
-            if (*(volatile int *)abort_flag) return false;
-            if (clock64() - t0 > limit) {
-                atomicExch(abort_flag, 1);
-                return false;
-            }
-        }
-        return true;
-    };
-    auto origin = [&](int id, int64_t *Y0, int64_t *X0) {
-        *Y0 = rh + (int64_t)(id / ntx) * TM;
-        *X0 = (int64_t)(id % ntx) * TX - p.xshift;
-    };
-
-    if (warp == 8) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            const uint32_t idesc = instr_desc(kFmtF16, TM, TN_);
-            const uint32_t lbo_a = (uint32_t)HS * 16;
-            const uint32_t b0 = smem_u32(B0), b1 = smem_u32(B1);
-            int k = 0;
-            for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++k) {
-                const int b = k & 1;
-                if (!bounded_wait(&full[b], (k >> 1) & 1, kWaitCycles)) break;
-                if (k >= 2 && !bounded_wait(&freeb[b], ((k - 2) >> 1) & 1, kWaitCycles)) break;
-                fence_after_thread_sync();
-                const uint64_t da_base = smem_desc(smem_u32(Ahi[b]), lbo_a, 128);
-                const uint64_t db_base = smem_desc(b0, 128, 256);
-                const uint64_t dlo_a = (uint64_t)((smem_u32(Alo[b]) - smem_u32(Ahi[b])) >> 4);
-                const uint64_t dlo_b = (uint64_t)((b1 - b0) >> 4);
-                const uint64_t kb_step_a = (uint64_t)2 * HS;  // two 8-value chunk columns
-                const uint64_t blk16 = kBlk >> 4;
-                const uint32_t dset = tmem + b * kSet;
-                uint32_t acc = 0;
-                for (int ai = 0; ai < lines; ++ai) {
-                    const int klo = p.kb_lo[ai], khi = p.kb_hi[ai];
-                    uint64_t da = da_base + (uint64_t)ai + (uint64_t)klo * kb_step_a;
-                    uint64_t db = db_base + (uint64_t)(ai * nkb + klo) * blk16;
-                    for (int kb = klo; kb <= khi; ++kb) {
-#pragma unroll
-                        for (int q = 0; q < NACC; ++q) {
-                            const uint32_t d = dset + q * TN_, dc = d + kCorr;
-                            const uint64_t daq = da + (uint64_t)(q * (TN_ / 8)) * HS;
-                            mma_f16(d, daq, db, idesc, acc);
-                            if (SPLIT) {
-                                mma_f16(dc, daq, db + dlo_b, idesc, acc);
-                                mma_f16(dc, daq + dlo_a, db, idesc, 1);
-                            }
-                        }
-                        acc = 1;
-                        da += kb_step_a;
-                        db += blk16;
-                    }
-                }
-                mma_commit(&done[b]);
-            }
-            if (k >= 1) wait_mbar_cycles(&done[(k - 1) & 1], ((k - 1) >> 1) & 1);
-            if (k >= 2) wait_mbar_cycles(&done[(k - 2) & 1], ((k - 2) >> 1) & 1);
-        }
-        __syncwarp();
-    } else {
-        // ------- loaders / converters (warps 0-7), epilogue (warps 0-3) -------
-        const int rows = TM + 2 * R, ncw = 2 * NCH;  // FP32 chunk columns of the window
-        auto prefetch = [&](int id, float *dst) {
-            int64_t Y0, X0;
-            origin(id, &Y0, &X0);
-            if (p.vec16) {
-                // one 16-byte copy per (row, FP32 chunk column); X0 - R is a
-                // multiple of 4, so each chunk lies wholly inside or outside its row
-                for (int row = warp; row < rows; row += 8) {
-                    const int64_t gy = Y0 - R + row;
-                    const bool rowok = gy >= 0 && gy < Ey;
-                    const float *grow = in + (rowok ? gy : 0) * Ex;
-                    for (int c = lane; c < ncw; c += 32) {
-                        const int64_t gx = X0 - R + 4 * c;
-                        const bool ok = rowok && gx >= 0 && gx < Ex;
-                        const uint32_t d = smem_u32(dst) + (uint32_t)(c * HS + row) * 16;
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d),
-                                     "l"(ok ? grow + gx : in), "r"(ok ? 16 : 0)
-                                     : "memory");
-                    }
-                }
-                return;
-            }
-            for (int row = warp; row < rows; row += 8) {
-                const int64_t gy = Y0 - R + row;
-                const bool rowok = gy >= 0 && gy < Ey;
-                for (int x = lane; x < 4 * ncw; x += 32) {
-                    const int64_t gx = X0 - R + x;
-                    const bool ok = rowok && gx >= 0 && gx < Ex;
-                    cu::cp_async_elem<4>(reinterpret_cast<unsigned char *>(dst) + (x / 4) * HS * 16 + row * 16 +
-                                             (x % 4) * 4,
-                                         ok ? in + gy * Ex + gx : in, ok);
-                }
-            }
-        };
-        // largest biased exponent of the chunks (or elements) this thread copied
-        auto own_max = [&](const float *src) -> int {
-            int mx = 0;
-            if (p.vec16) {
-                for (int row = warp; row < rows; row += 8)
-                    for (int c = lane; c < ncw; c += 32) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(reinterpret_cast<const unsigned char *>(src) +
-                                                                         (size_t)(c * HS + row) * 16);
-                        mx = max(mx, (int)max(max((v.x >> 23) & 255u, (v.y >> 23) & 255u),
-                                              max((v.z >> 23) & 255u, (v.w >> 23) & 255u)));
-                    }
-                return mx;
-            }
-            for (int row = warp; row < rows; row += 8)
-                for (int x = lane; x < 4 * ncw; x += 32) {
-                    const uint32_t v = *reinterpret_cast<const uint32_t *>(
-                        reinterpret_cast<const unsigned char *>(src) + (size_t)((x / 4) * HS + row) * 16 + (x % 4) * 4);
-                    mx = max(mx, (int)((v >> 23) & 255u));
-                }
-            return mx;
-        };
-        auto epilogue = [&](int id, uint32_t set_base, int eu) {
-            int64_t Y0, X0;
-            origin(id, &Y0, &X0);
-            const int m = warp * 32 + lane;
-            const int64_t gy = Y0 + m, iy = gy - rh;
-            const bool rowok = iy < ny && iy >= p.band && ny - 1 - iy >= p.band;
-            const uint32_t lane_base = set_base + ((uint32_t)(warp * 32) << 16);
-            // 2^(eu + ew) as two in-range powers of two
-            const int e = eu + p.ew, e1 = e / 2, e2 = e - e1;
-            const float sc1 = pow2f(max(-126, min(127, e1))), sc2 = pow2f(max(-126, min(127, e2)));
-            for (int q = 0; q < NACC; ++q) {
-#pragma unroll
-                for (int h = 0; h < TN_ / 8; ++h) {
-                    uint32_t v[8], c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                    __syncwarp();
-                    tmem_ld_32x32b_x8(lane_base + q * TN_ + h * 8, v);
-                    if (SPLIT) tmem_ld_32x32b_x8(lane_base + kCorr + q * TN_ + h * 8, c);
-                    tmem_ld_wait();
-                    if (!rowok) continue;
-                    float f[8];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        f[j] = (__uint_as_float(v[j]) + (SPLIT ? __uint_as_float(c[j]) : 0.0f)) * sc1 * sc2;
-                    const int64_t gx0 = X0 + q * TN_ + h * 8;
-                    float *dst = out + gy * Ex + gx0;
-                    const bool fullrow = gx0 >= rh + p.band && gx0 + 7 < Ex - rh - p.band;
-                    const uintptr_t al = reinterpret_cast<uintptr_t>(dst) & 15;
-                    if (fullrow && al == 0) {
-                        reinterpret_cast<float4 *>(dst)[0] = make_float4(f[0], f[1], f[2], f[3]);
-                        reinterpret_cast<float4 *>(dst)[1] = make_float4(f[4], f[5], f[6], f[7]);
-                    } else if (fullrow && (al & 7) == 0) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            reinterpret_cast<float2 *>(dst)[j] = make_float2(f[2 * j], f[2 * j + 1]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int64_t ix = gx0 + j - rh;
-                            if (ix >= p.band && ix < nx - p.band) dst[j] = f[j];
-                        }
-                    }
-                }
-            }
-        };
-
-        int k = 0, prev = -1, prev_eu = 0;
-        if ((int)blockIdx.x < ntiles) prefetch(blockIdx.x, raw[0]);
-        cu::cp_async_commit();
-        bool ok = true;
-        for (int id = blockIdx.x; id < ntiles; id += gridDim.x, ++k) {
-            const int b = k & 1;
-            // this tile's copies are in (each thread waits for its own), then its
-            // exponent is exchanged: the mbarrier also publishes every copy
-            cu::cp_async_wait_group<0>();
-            const int mx = __reduce_max_sync(0xffffffffu, (unsigned)own_max(raw[b]));
-            if (lane == 0) wmax[b * 8 + warp] = mx;
-            __syncwarp();
-            mbar_arrive(&maxb[b]);
-            if (!bounded_wait(&maxb[b], (k >> 1) & 1, kWaitCycles)) {
-                ok = false;
-                break;
-            }
-            int emax = wmax[b * 8];
-#pragma unroll
-            for (int w = 1; w < 8; ++w) emax = max(emax, wmax[b * 8 + w]);
-            // the next tile's loads go out first (into the other raw buffer, last
-            // read before this tile's exponent exchange)
-            const int nid = id + gridDim.x;
-            if (nid < ntiles) prefetch(nid, raw[b ^ 1]);
-            cu::cp_async_commit();
-            // |x| < 2^(emax - 126): scale by 2^-eu, eu = emax - 126 (zero tiles: 1)
-            const int eu = emax > 0 ? emax - 126 : -125;
-            const float xs = pow2f(max(-126, min(127, -eu)));
-            const int quads = NCH * HS;  // 8-value chunks of the FP16 buffer
-            for (int i = tid; i < quads; i += 256) {
-                const int c = i / HS, row = i - (i / HS) * HS;
-                const float4 u0 = *reinterpret_cast<const float4 *>(reinterpret_cast<const unsigned char *>(raw[b]) +
-                                                                    (size_t)(2 * c * HS + row) * 16);
-                const float4 u1 = *reinterpret_cast<const float4 *>(reinterpret_cast<const unsigned char *>(raw[b]) +
-                                                                    (size_t)((2 * c + 1) * HS + row) * 16);
-                const float x[8] = {u0.x * xs, u0.y * xs, u0.z * xs, u0.w * xs, u1.x * xs, u1.y * xs, u1.z * xs,
-                                    u1.w * xs};
-                __half2 hv[4], lv[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    hv[j] = __floats2half2_rn(x[2 * j], x[2 * j + 1]);
-                    if (SPLIT) {
-                        const float2 hf = __half22float2(hv[j]);
-                        lv[j] = __floats2half2_rn(x[2 * j] - hf.x, x[2 * j + 1] - hf.y);
-                    }
-                }
-                const size_t off = (size_t)(c * HS + row) * 16;
-                *reinterpret_cast<uint4 *>(Ahi[b] + off) = *reinterpret_cast<const uint4 *>(hv);
-                if (SPLIT) *reinterpret_cast<uint4 *>(Alo[b] + off) = *reinterpret_cast<const uint4 *>(lv);
-            }
-            fence_proxy_async_smem();
-            mbar_arrive(&full[b]);
-            if (k >= 1) {  // tile k-1: its MMAs filled accumulator set b^1
-                if (!bounded_wait(&done[b ^ 1], ((k - 1) >> 1) & 1, kWaitCycles)) {
-                    ok = false;
-                    break;
-                }
-                fence_after_thread_sync();
-                if (warp < 4) {
-                    epilogue(prev, tmem + (b ^ 1) * kSet, prev_eu);
-                    fence_before_thread_sync();
-                    mbar_arrive(&freeb[b ^ 1]);
-                }
-            }
-            prev = id;
-            prev_eu = eu;
-        }
-        if (ok && prev >= 0) {
-            const int lb = (k - 1) & 1;
-            ok = bounded_wait(&done[lb], ((k - 1) >> 1) & 1, kWaitCycles);
-            fence_after_thread_sync();
-            if (ok && p.debug_unmet) ok = bounded_wait(&done[lb], (((k - 1) >> 1) & 1) ^ 1, kDebugWaitCycles);
-            if (ok && warp < 4) epilogue(prev, tmem + lb * kSet, prev_eu);
-        }
-        cu::cp_async_wait_group<0>();
-        if (!ok) atomicExch(abort_flag, 1);
-    }
-    fence_before_thread_sync();
-    __syncthreads();
-    if (tid == 0 && *(volatile int *)abort_flag) atomicExch(&g_tc_error, 1);
-    if (warp == 0) tmem_dealloc(tmem, kCols);
-}
-
 }  // namespace tcs
 
 // ---------------------------------------------------------------------------
@@ -1053,38 +514,6 @@ stencil_status fill_params(const Plan &p, int t, int n_tile, int k_inst, TcParam
     tp->Ey = p.ext[1];
     tp->Ex = p.ext[2];
     return STENCIL_OK;
-}
-
-template <int PREC, int NACC>
-stencil_status launch_tc2d(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
-{
-    using namespace tcs;
-    constexpr int ES = Elem<PREC>::bytes, E = 16 / ES, KI = 2 * E, TX = NACC * TN;
-    TcParams tp;
-    TcLines L;
-    stencil_status s = fill_params(p, t, TN, KI, &tp, &L);
-    if (s != STENCIL_OK) return s;
-    const int R = tp.R;
-    tp.hs = TM + 2 * R;
-    if (tp.hs % 2 == 0) tp.hs += 1;  // odd chunk-column height: conflict-free staging stores
-    tp.nch = (TN * (NACC - 1) + L.kext) / E;
-    const bool split = PREC != P_TF32;
-    const size_t a_bytes = (size_t)tp.nch * tp.hs * 16;
-    const size_t b_bytes = (size_t)(2 * R + 1) * L.nkb * 256;
-    size_t smem = (a_bytes + b_bytes) * (split ? 2 : 1);
-    const size_t stage = (size_t)TM * (TX + 4) * 4;
-    if (smem < stage) smem = stage;
-    smem += 128;  // TMEM address and mbarrier in front of the operands
-    if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core tile does not fit in shared memory");
-    auto kern = tc2d_sweep<PREC, NACC>;
-    s = ensure_smem((const void *)kern, smem);
-    if (s != STENCIL_OK) return s;
-    const int64_t ny = p.dims[1], nx = p.dims[2];
-    dim3 grid((unsigned)((nx + TX - 1) / TX), (unsigned)((ny + TM - 1) / TM));
-    kern<<<grid, 128, smem, st>>>((const float *)in, (float *)out, tp);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_sweep launch");
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime
@@ -1165,51 +594,6 @@ stencil_status launch_tc2d_ws_n(const Plan &p, const void *in, void *out, int t,
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_ws launch");
 }
 
-template <int PREC, int TN_, int NACC>
-stencil_status launch_tc2d_wsh_n(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
-{
-    using namespace tcs;
-    constexpr int TX = NACC * TN_;
-    TcParams tp;
-    TcLines L;
-    stencil_status s = fill_params(p, t, TN_, 16, &tp, &L);
-    if (s != STENCIL_OK) return s;
-    const int R = tp.R;
-    tp.hs = (TM + 2 * R) | 1;
-    tp.nch = (TN_ * (NACC - 1) + L.kext) / 8;
-    double wmax = 0;
-    for (int i = 0; i < (2 * R + 1) * (2 * R + 1); i++) wmax = std::max(wmax, std::fabs(tp.w[i]));
-    tp.ew = 0;
-    if (wmax > 0) std::frexp(wmax, &tp.ew);  // wmax < 2^ew
-    const size_t smem = tc_wsh_smem(R, L.nkb, TN_, NACC, PREC == P_F16X3);
-    if (smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "FP16 tensor-core tile does not fit in shared memory");
-    auto kern = tc2d_wsh<PREC, TN_, NACC>;
-    s = ensure_smem((const void *)kern, smem);
-    if (s != STENCIL_OK) return s;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    tp.vec16 = (p.ext[2] % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
-    tp.xshift = tp.vec16 ? (4 - R % 4) % 4 : 0;
-    const int64_t nty = (p.dims[1] + TM - 1) / TM, ntx = (p.ext[2] + tp.xshift + TX - 1) / TX;
-    const int64_t ntiles = nty * ntx;
-    if (ntiles > 0x7fffffff) return fail(STENCIL_ERR_UNSUPPORTED, "too many tiles");
-    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, sms);
-    kern<<<grid, 288, smem, st>>>((const float *)in, (float *)out, tp, (int)ntiles, (int)ntx);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "tc2d_wsh launch");
-}
-
-template <int PREC>
-stencil_status launch_tc2d_wsh(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
-{
-    const int tn = tc_wsh_ntile(p.pat.shape, p.pat.r, t, PREC == tcs::P_F16X3);
-    if (tn == 32) return launch_tc2d_wsh_n<PREC, 32, 2>(p, in, out, t, st);
-    if (tn == 16) return launch_tc2d_wsh_n<PREC, 16, 2>(p, in, out, t, st);
-    return fail(STENCIL_ERR_UNSUPPORTED, "FP16 tensor-core tile does not fit in shared memory");
-}
-
 // Widest MMA N whose operands fit in shared memory (the rule the dispatcher
 // uses to report S, tc_ws_ntile).
 template <int PREC>
@@ -1263,20 +647,10 @@ stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, 
         switch (p.precision) {
         case STENCIL_PREC_TF32: s = launch_tc2d_ws<tcs::P_TF32>(p, in, out, t, st); break;
         case STENCIL_PREC_TF32X3: s = launch_tc2d_ws<tcs::P_TF32X3>(p, in, out, t, st); break;
-        case STENCIL_PREC_BF16X3:
-            // the wide form where its operands fit, else the N = 8 synchronous kernel
-            if (tc_wide_nrows(p.pat.r, t, true) > 0) s = launch_wide_sweep(p, in, out, t, true, true, st);
-            else s = launch_tc2d<tcs::P_BF16X3, 8>(p, in, out, t, st);
-            break;
-        case STENCIL_PREC_F16:
-        case STENCIL_PREC_F16X3: {
-            // the wide form where its operands fit, else N = 32 / 16 tiles
-            const bool split = p.precision == STENCIL_PREC_F16X3;
-            if (tc_wide_nrows(p.pat.r, t, split) > 0) s = launch_wide_sweep(p, in, out, t, split, false, st);
-            else if (split) s = launch_tc2d_wsh<tcs::P_F16X3>(p, in, out, t, st);
-            else s = launch_tc2d_wsh<tcs::P_F16>(p, in, out, t, st);
-            break;
-        }
+        // the FP16 / BF16 forms: the wide kernel (a tile fits for every t r <= 12)
+        case STENCIL_PREC_BF16X3: s = launch_wide_sweep(p, in, out, t, true, true, st); break;
+        case STENCIL_PREC_F16: s = launch_wide_sweep(p, in, out, t, false, false, st); break;
+        case STENCIL_PREC_F16X3: s = launch_wide_sweep(p, in, out, t, true, false, st); break;
         default: return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: precision");
         }
     }

@@ -130,7 +130,7 @@ struct Op<true> {
     }
 };
 
-template <bool SPLIT, int NR, int NKB, bool BF>
+template <bool SPLIT, int NR, int NKB, bool BF, int NBUF>
 __global__ void __launch_bounds__(kThreads, 1)
     tc2d_wide(const float *__restrict__ in, float *__restrict__ out, const __grid_constant__ WideParams p,
               int ntiles, int ntx)
@@ -154,7 +154,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *Whi = smem + kHeader;
     unsigned char *Wlo = Whi + strip_bytes;
     unsigned char *ibase = Whi + strip_bytes * (SPLIT ? 2 : 1);
-    // operand buffer b: hi at ibase + b in_bytes, lo (f16x3) 2 in_bytes further
+    // operand buffer b (b = 0 when NBUF = 1): hi at ibase + b in_bytes, lo
+    // (the 3-product forms) NBUF in_bytes further
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t Ey = p.Ey, Ex = p.Ex, rh = p.rh;
     const int64_t ny = Ey - 2 * rh, nx = Ex - 2 * rh;
@@ -225,8 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!bounded_wait(&full[b], (k >> 1) & 1, kWaitCycles)) break;
                 if (k >= 2 && !bounded_wait(&accfree[b], ((k - 2) >> 1) & 1, kWaitCycles)) break;
                 fence_after_thread_sync();
-                const uint64_t b0 = smem_desc(smem_u32(ibase + b * in_bytes), (uint32_t)HS * 16, 128);
-                const uint64_t dlo_b = (uint64_t)((2 * in_bytes) >> 4);
+                const uint64_t b0 = smem_desc(smem_u32(ibase + (NBUF == 2 ? b : 0) * in_bytes), (uint32_t)HS * 16, 128);
+                const uint64_t dlo_b = (uint64_t)((NBUF * in_bytes) >> 4);
                 const uint32_t d = tmem + (uint32_t)(b * NR);
                 uint32_t acc = 0;
                 for (int ai = 0; ai < lines; ++ai) {
@@ -346,17 +347,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             // |x| < 2^(emax - 126): x 2^es < 2^15 with es = 141 - emax (clamped)
             const int es = max(-126, min(127, 141 - emax));
             const float xs = pow2f(es);
-            // operand buffer b is free once the MMAs of tile k - 2 completed
-            if (k >= 2 && !bounded_wait(&done[b], ((k - 2) >> 1) & 1, kWaitCycles)) break;
+            // the operand buffer is free once the MMAs of tile k - NBUF completed
+            if (NBUF == 2 && k >= 2 && !bounded_wait(&done[b], ((k - 2) >> 1) & 1, kWaitCycles)) break;
+            if (NBUF == 1 && k >= 1 && !bounded_wait(&done[b ^ 1], ((k - 1) >> 1) & 1, kWaitCycles)) break;
             // publish the scale: slot k & 3 was last read by the epilogue of tile
             // k - 4, which finished before the MMAs of tile k - 2 could start
+            // (and those precede the MMAs of tile k - NBUF waited for above)
             if (tid == 0) {
                 eus[k & 3] = es;
                 mbar_arrive(&eub[k & 3]);
             }
             // pass 2: scale, convert, store 4 FP16/BF16 values (8 bytes) per float4
             {
-                unsigned char *hi = ibase + b * in_bytes, *lo = hi + 2 * in_bytes;
+                unsigned char *hi = ibase + (NBUF == 2 ? b : 0) * in_bytes, *lo = hi + NBUF * in_bytes;
                 int row = tid / F4, c4 = tid % F4;
                 for (int i0 = tid; i0 < items; i0 += kBatch * kLoaders) {
                     float4 vb[kBatch];
@@ -462,13 +465,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 namespace {
 
-template <bool SPLIT, int NR, int NKB, bool BF>
+template <bool SPLIT, int NR, int NKB, bool BF, int NBUF>
 stencil_status launch_wide_n(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
     using namespace wide;
     const int r = p.pat.r, R = t * r;
     if (R > kMaxR) return fail(STENCIL_ERR_UNSUPPORTED, "wide FP16 path: fused radius t*r must be <= 12");
-    const WideGeom g = tc_wide_geom(R, NR, SPLIT);
+    const WideGeom g = tc_wide_geom(R, NR, SPLIT, NBUF);
     if (g.smem > 227 * 1024) return fail(STENCIL_ERR_UNSUPPORTED, "wide FP16 tile does not fit in shared memory");
     if (g.nkb != NKB) return fail(STENCIL_ERR_INTERNAL, "wide FP16 path: K blocks");
     const TcLines L = tc_lines_2d(p.pat.shape, r, t, TM, KI);
@@ -503,7 +506,7 @@ stencil_status launch_wide_n(const Plan &p, const void *in, void *out, int t, cu
     wp.Ex = p.ext[2];
     wp.vec16 = (p.ext[2] % 4 == 0) && (reinterpret_cast<uintptr_t>(in) % 16 == 0);
     wp.xshift = wp.vec16 ? (4 - R % 4) % 4 : 0;  // (tile start - R) a multiple of 4
-    auto kern = tc2d_wide<SPLIT, NR, NKB, BF>;
+    auto kern = tc2d_wide<SPLIT, NR, NKB, BF, NBUF>;
     stencil_status s = ensure_smem((const void *)kern, g.smem);
     if (s != STENCIL_OK) return s;
     int dev = 0, sms = 0;
@@ -524,21 +527,25 @@ stencil_status launch_wide_n(const Plan &p, const void *in, void *out, int t, cu
 stencil_status launch_wide_sweep(const Plan &p, const void *in, void *out, int t, bool split, bool bf16,
                                  cudaStream_t st)
 {
-    const int nr = tc_wide_nrows(p.pat.r, t, split);
-    const int nkb = tc_wide_geom(t * p.pat.r, nr > 0 ? nr : 64, split).nkb;  // 9 (R <= 8) or 10
-    // the (N, K blocks) pairs tc_wide_nrows can pick
-    if (split && bf16) {  // hi and lo operands: N = 256 never fits
-        if (nr == 128 && nkb == 9) return launch_wide_n<true, 128, 9, true>(p, in, out, t, st);
-        if (nr == 64 && nkb == 9) return launch_wide_n<true, 64, 9, true>(p, in, out, t, st);
-        if (nr == 64 && nkb == 10) return launch_wide_n<true, 64, 10, true>(p, in, out, t, st);
-    } else if (split) {
-        if (nr == 128 && nkb == 9) return launch_wide_n<true, 128, 9, false>(p, in, out, t, st);
-        if (nr == 64 && nkb == 9) return launch_wide_n<true, 64, 9, false>(p, in, out, t, st);
-        if (nr == 64 && nkb == 10) return launch_wide_n<true, 64, 10, false>(p, in, out, t, st);
+    const WideTile wt = tc_wide_tile(p.pat.r, t, split);
+    const int nr = wt.nr, nb = wt.nbuf;
+    const int nkb = tc_wide_geom(t * p.pat.r, 128, split).nkb;  // 9 (R <= 8) or 10
+    // the (N, K blocks, buffers) triples tc_wide_tile can pick
+    if (split) {
+#define GBS_WIDE_SPLIT(BFV)                                                                                   \
+    if (nr == 128 && nkb == 9 && nb == 2) return launch_wide_n<true, 128, 9, BFV, 2>(p, in, out, t, st);     \
+    if (nr == 128 && nkb == 9 && nb == 1) return launch_wide_n<true, 128, 9, BFV, 1>(p, in, out, t, st);     \
+    if (nr == 128 && nkb == 10 && nb == 1) return launch_wide_n<true, 128, 10, BFV, 1>(p, in, out, t, st);
+        if (bf16) {
+            GBS_WIDE_SPLIT(true)
+        } else {
+            GBS_WIDE_SPLIT(false)
+        }
+#undef GBS_WIDE_SPLIT
     } else if (!bf16) {
-        if (nr == 256 && nkb == 9) return launch_wide_n<false, 256, 9, false>(p, in, out, t, st);
-        if (nr == 256 && nkb == 10) return launch_wide_n<false, 256, 10, false>(p, in, out, t, st);
-        if (nr == 128 && nkb == 10) return launch_wide_n<false, 128, 10, false>(p, in, out, t, st);
+        if (nr == 256 && nkb == 9 && nb == 2) return launch_wide_n<false, 256, 9, false, 2>(p, in, out, t, st);
+        if (nr == 256 && nkb == 10 && nb == 2) return launch_wide_n<false, 256, 10, false, 2>(p, in, out, t, st);
+        if (nr == 128 && nkb == 10 && nb == 2) return launch_wide_n<false, 128, 10, false, 2>(p, in, out, t, st);
     }
     return fail(STENCIL_ERR_UNSUPPORTED, "wide FP16 tile does not fit in shared memory");
 }

@@ -196,13 +196,9 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
         g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
-    if (d == 2 && dtype == STENCIL_F32 && precision == STENCIL_PREC_BF16X3 && tc_wide_nrows(r, t, true) > 0)
-        g.n_tile = 128;  // the wide kernel (else the N = 8 synchronous kernel)
-    if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3)) {
-        // the wide kernel: 128 output columns per MMA (M), else N = 32 / 16 tiles
-        const bool split = precision == STENCIL_PREC_F16X3;
-        g.n_tile = tc_wide_nrows(r, t, split) > 0 ? 128 : std::max(16, tc_wsh_ntile(shape, r, t, split));
-    }
+    if (d == 2 && dtype == STENCIL_F32 &&
+        (precision == STENCIL_PREC_BF16X3 || precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3))
+        g.n_tile = 128;  // the wide kernel: 128 output columns per MMA (its M)
     if (d == 2 && path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
         // mma.sp m16n8k16: 16 output columns per block, logical K 16
         SpLayout L = sp_layout_2d(shape, r, t);
@@ -281,25 +277,18 @@ static double beta_of(int precision, int slices = 0)
 // per cycle) is longer.  A sweep kernel therefore runs at
 //     cycles per output = max(MMAs per output * cost per MMA,
 //                             worker cycles per output)
-// (their sum for the synchronous BF16x3 kernel), the second term being the
-// CUDA-core work of staging, rounding or cutting the input and draining the
-// accumulators, measured per kernel at t = 1 on GB300 at 2070 MHz.  The
+// (their sum for the wide FP16 / BF16 kernel, whose staging and epilogue
+// overlap its MMAs only in part), the second term being the CUDA-core work
+// of staging, rounding or cutting the input and draining the accumulators,
+// measured per kernel on GB300 at 2070 MHz.  The
 // instruction roof t * SMs * clock / cycles per output caps the paper's
 // tensor-core roof (Eq. 12) for the dispatcher.
 // ---------------------------------------------------------------------------
 constexpr double kMmaCycles = 90.0;        // per tcgen05.mma, M = 128, N <= ~176
 constexpr double kWorkerTf32 = 1.30;       // tc2d_ws TF32: in-place rounding, staging, epilogue
 constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
-constexpr double kWorkerF16 = 2.20;        // tc2d_wsh F16: staging, exponent, conversion, epilogue
-constexpr double kWorkerF16x3 = 2.40;      // tc2d_wsh F16x3: + the lo parts
-constexpr double kMmaCyclesWsh = 110.0;    // tc2d_wsh: its MMAs share shared memory with the conversion
 constexpr double kWorkerWide = 0.45;       // tc2d_wide, one product: loads, conversion, epilogue (added to the MMAs)
-constexpr double kWorkerWideSplit = 0.28;  // tc2d_wide, three products (128- / 64-row tiles)
-// tc2d_sweep BF16x3 runs one tile per CTA with several CTAs per SM, whose
-// MMAs interleave: 2.65 cycles per output plus 47.6 per MMA of an output
-// (fitted to Box-2D2R at t = 1..4 within 10 %)
-constexpr double kWorkerBf16x3 = 2.65;
-constexpr double kBf16x3MmaCycles = 47.6;
+constexpr double kWorkerWideSplit = 0.28;  // tc2d_wide, three products (128-row tiles, one or two buffers)
 constexpr double kWorkerSplit = 4.06;      // tc2d_split: FP64 load, exponent, digit cut, recombination
 // sptc2d_sweep issues warp-level mma.sp between its staging and epilogue
 // work, so the two add: 0.92 cycles per output plus 3.15 per sparse
@@ -351,27 +340,15 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
         const double mma = blocks * products / (128.0 * nr) * std::max(kMmaCycles, 128.0 * nr * 16 / 4096.0);
         // measured: the staging and epilogue overlap the MMAs only in part
         per_out = mma + (prec == STENCIL_PREC_F16 ? kWorkerWide : kWorkerWideSplit);
-    } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3)) {
-        const int n = tc_wsh_ntile(shape, r, t, prec == STENCIL_PREC_F16X3);
-        if (n == 0) return 0;
-        const TcLines L = tc_lines_2d(shape, r, t, n, 16);
-        double blocks = 0;
-        for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
-        const double products = prec == STENCIL_PREC_F16 ? 1.0 : 3.0;
-        const double mma = blocks * products / (128.0 * n) * std::max(kMmaCyclesWsh, 128.0 * n * 16 / 4096.0);
-        per_out = std::max(mma, prec == STENCIL_PREC_F16 ? kWorkerF16 : kWorkerF16x3);
-    } else if (p.dtype == STENCIL_F32) {
-        const bool bf = prec == STENCIL_PREC_BF16X3;
-        const int n = bf ? 8 : tc_ws_ntile(shape, r, t, prec == STENCIL_PREC_TF32X3);
-        const int k = bf ? 16 : 8;
-        const TcLines L = tc_lines_2d(shape, r, t, n, k);
+    } else if (p.dtype == STENCIL_F32 && (prec == STENCIL_PREC_TF32 || prec == STENCIL_PREC_TF32X3)) {
+        const int n = tc_ws_ntile(shape, r, t, prec == STENCIL_PREC_TF32X3);
+        const TcLines L = tc_lines_2d(shape, r, t, n, 8);
         double blocks = 0;
         for (size_t a = 0; a < L.kb_lo.size(); a++) blocks += std::max(0, L.kb_hi[a] - L.kb_lo[a] + 1);
         const double products = prec == STENCIL_PREC_TF32 ? 1.0 : 3.0;
-        const double cost = std::max(kMmaCycles, 128.0 * n * k / (bf ? 4096.0 : 2048.0));
+        const double cost = std::max(kMmaCycles, 128.0 * n * 8 / 2048.0);
         const double mma = blocks * products / (128.0 * n) * cost;
-        if (bf) per_out = kWorkerBf16x3 + blocks * products / (128.0 * n) * kBf16x3MmaCycles;
-        else per_out = std::max(mma, prec == STENCIL_PREC_TF32 ? kWorkerTf32 : kWorkerTf32x3);
+        per_out = std::max(mma, prec == STENCIL_PREC_TF32 ? kWorkerTf32 : kWorkerTf32x3);
     } else {
         return 0;
     }
@@ -489,17 +466,12 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                         c.tile[1] = 128;
                         c.tile[2] = 16 * split_nacc(t * r, slices);
                     }
-                    if (prec == STENCIL_PREC_BF16X3 && tc_wide_nrows(r, t, true) > 0) {
-                        c.tile[1] = tc_wide_nrows(r, t, true);
+                    if (prec == STENCIL_PREC_BF16X3 || prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
+                        // the wide kernel: output rows (MMA N) x 128 columns
+                        const int nr = tc_wide_nrows(r, t, prec != STENCIL_PREC_F16);
+                        if (nr == 0) continue;  // t r > 12
+                        c.tile[1] = nr;
                         c.tile[2] = 128;
-                    }
-                    if (prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
-                        const bool split = prec == STENCIL_PREC_F16X3;
-                        const int nr = tc_wide_nrows(r, t, split);
-                        const int tn = tc_wsh_ntile(shape, r, t, split);
-                        if (nr == 0 && tn == 0) continue;  // the tile does not fit
-                        c.tile[1] = nr > 0 ? nr : 128;
-                        c.tile[2] = nr > 0 ? 128 : 2 * tn;
                     }
                     TcGeometry g = tc_geometry(shape, d, r, t, p->dtype, prec, path);
                     ModelOut m = model_eval(shape, d, r, t, D, g.sparsity, beta_of(prec, slices), P_cu,

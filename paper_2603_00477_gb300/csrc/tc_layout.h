@@ -85,30 +85,6 @@ inline int tc_ws_ntile(int shape, int r, int t, bool split)
     return 8;
 }
 
-// Shared memory of the FP16 warp-specialised kernel (tc2d_wsh) at MMA N = n,
-// nacc column blocks per tile, nkb K blocks of 16 per line: a 256-byte
-// header, the FP16 Toeplitz blocks (x2 split), two FP32 staging buffers and
-// two FP16 operand buffers (x2 split) of 128 + 2R rows (odd) by the window of
-// (nacc - 1) n + 16 nkb columns.
-inline size_t tc_wsh_smem(int R, int nkb, int n, int nacc, bool split)
-{
-    const size_t hs = (size_t)((128 + 2 * R) | 1);
-    const size_t nch = (size_t)(n * (nacc - 1) + 16 * nkb) / 8;
-    const size_t raw = 2 * nch * hs * 16, a = nch * hs * 16;
-    const size_t b = (size_t)(2 * R + 1) * nkb * (n / 8) * 256;
-    return 256 + b * (split ? 2 : 1) + 2 * raw + a * (split ? 4 : 2);
-}
-
-// MMA N of the FP16 kernel: 32 if its tiles fit in 227 KB, else 16, else 0.
-inline int tc_wsh_ntile(int shape, int r, int t, bool split)
-{
-    for (int n : {32, 16}) {
-        TcLines L = tc_lines_2d(shape, r, t, n, 16);
-        if (tc_wsh_smem(t * r, L.nkb, n, 2, split) <= 227 * 1024) return n;
-    }
-    return 0;
-}
-
 // Wide FP16 kernel (tc2d_wide): the Toeplitz factor of line a is the A
 // operand over M = 128 output columns (stored in reverse order, so that
 // A[m'][k] depends on k + m' only) and K = 16 nkb window columns,
@@ -118,33 +94,50 @@ inline int tc_wsh_ntile(int shape, int r, int t, bool split)
 // matrices 15 .. (127 + 2R) / 8, so consecutive lines' strips are placed
 // max(2 nkb, (127 + 2R) / 8 + 1) core matrices apart and overlap in zeros.
 struct WideGeom {
-    int nkb, strip_len, delta, hs;
+    int nkb, strip_len, delta, hs, nbuf;
     size_t strip_bytes, in_bytes, smem;
 };
 
-inline WideGeom tc_wide_geom(int R, int nr, bool split)
+inline WideGeom tc_wide_geom(int R, int nr, bool split, int nbuf = 2)
 {
     WideGeom g;
     g.nkb = (128 + 2 * R + 15) / 16;
     g.strip_len = 2 * g.nkb + 15;
     g.delta = std::max(2 * g.nkb, (127 + 2 * R) / 8 + 1);
     g.hs = (nr + 2 * R) | 1;  // odd chunk-column height: conflict-free staging stores
+    g.nbuf = nbuf;
     g.strip_bytes = (size_t)(2 * R * g.delta + g.strip_len) * 128;
     g.in_bytes = (size_t)(2 * g.nkb) * g.hs * 16;
-    // 1 KB header, weight strips (hi, lo), two input buffers (hi, lo)
-    g.smem = 1024 + (g.strip_bytes + 2 * g.in_bytes) * (split ? 2 : 1);
+    // 1 KB header, weight strips (hi, lo), nbuf input buffers (hi, lo)
+    g.smem = 1024 + (g.strip_bytes + nbuf * g.in_bytes) * (split ? 2 : 1);
     return g;
 }
 
-// Output rows per tile (MMA N) of the wide kernel: the largest of 256, 128
-// and 64 whose operands fit in 227 KB; 0 if none does (R > 12 or no fit).
-inline int tc_wide_nrows(int r, int t, bool split)
+// Tile of the wide kernel: output rows (MMA N) and input buffers -- the
+// first of (256, 2), (128, 2), (128, 1) whose operands fit in 227 KB (double
+// buffering overlaps the next tile's conversion with this tile's MMAs; one
+// buffer keeps N = 128 for the hi + lo forms at R = 7 .. 12).  Every R <= 12
+// fits; nr = 0 beyond.
+struct WideTile {
+    int nr = 0, nbuf = 0;
+};
+
+inline WideTile tc_wide_tile(int r, int t, bool split)
 {
-    if (t * r > 12) return 0;
-    for (int nr : {256, 128, 64})
-        if (tc_wide_geom(t * r, nr, split).smem <= 227 * 1024) return nr;
-    return 0;
+    WideTile w;
+    if (t * r > 12) return w;
+    const int cand[3][2] = {{256, 2}, {128, 2}, {128, 1}};
+    for (auto &c : cand)
+        if (tc_wide_geom(t * r, c[0], split, c[1]).smem <= 227 * 1024) {
+            w.nr = c[0];
+            w.nbuf = c[1];
+            return w;
+        }
+    return w;
 }
+
+// Output rows per tile (MMA N) of the wide kernel, 0 if no tile fits.
+inline int tc_wide_nrows(int r, int t, bool split) { return tc_wide_tile(r, t, split).nr; }
 
 // ---------------------------------------------------------------------------
 // 2:4-structured sparse form (paper Sec. 4.3), TF32 1:2 on mma.sp m16n8k16.

@@ -73,7 +73,7 @@ CASES = [
     ("star", 2, (190, 260), 6, 3, "f32", "f16"),
     ("box", 1, (130, 140), 1, 1, "f32", "f16x3"),
     ("box", 2, (300, 500), 5, 2, "f32", "f16x3"),      # remainder sweep t' = 1; more tiles than SMs
-    ("box", 3, (140, 75), 5, 2, "f32", "f16x3"),       # R = 6: N = 16
+    ("box", 3, (140, 75), 5, 2, "f32", "f16x3"),       # R = 6, remainder sweep t' = 1
     ("star", 1, (128, 128), 7, 4, "f32", "f16x3"),
     ("box", 1, (5, 7), 3, 3, "f32", "f16"),            # grid smaller than the band
     # the wide FP16 kernel with more tiles than SMs (each persistent CTA
@@ -81,7 +81,13 @@ CASES = [
     ("box", 2, (4000, 4000), 6, 2, "f32", "f16"),       # 16 x 32 tiles of 256 x 128
     ("star", 3, (3000, 3500), 8, 4, "f32", "f16"),      # R = 12: 128-row tiles
     ("box", 1, (2000, 3001), 9, 4, "f32", "f16x3"),     # R = 4, 128-row tiles, unaligned rows
-    ("box", 2, (700, 900), 4, 4, "f32", "f16x3"),       # R = 8: 64-row tiles
+    ("box", 2, (700, 900), 4, 4, "f32", "f16x3"),       # R = 8: 128-row tiles, one operand buffer
+    # one operand buffer (hi + lo forms at R = 7 .. 12) with more tiles than
+    # SMs: each CTA converts a tile only after the previous tile's MMAs
+    ("box", 2, (2000, 2100), 8, 4, "f32", "bf16x3"),    # R = 8, 272 tiles
+    ("box", 5, (2100, 1900), 4, 2, "f32", "f16x3"),     # R = 10, 10 K blocks
+    ("star", 3, (1700, 2300), 8, 4, "f32", "bf16x3"),   # R = 12
+    ("box", 7, (1000, 1000), 2, 1, "f32", "f16x3"),     # R = 7 without fusion
 ]
 
 

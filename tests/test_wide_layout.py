@@ -33,14 +33,14 @@ def lib():
     return B.load()
 
 
-def geom(R, nr, split):
+def geom(R, nr, split, nbuf=2):
     nkb = (128 + 2 * R + 15) // 16
     strip_len = 2 * nkb + 15
     delta = max(2 * nkb, (127 + 2 * R) // 8 + 1)
     hs = (nr + 2 * R) | 1
     strip_bytes = (2 * R * delta + strip_len) * 128
     in_bytes = 2 * nkb * hs * 16
-    smem = 1024 + (strip_bytes + 2 * in_bytes) * (2 if split else 1)
+    smem = 1024 + (strip_bytes + nbuf * in_bytes) * (2 if split else 1)
     return nkb, delta, hs, strip_bytes, smem
 
 
@@ -110,20 +110,25 @@ def test_strip_operands_are_the_toeplitz_blocks(shape, r, t):
     assert max(hi) * 2 + 1 < 2 * nkb
 
 
-def test_wide_tiles_fit_and_fall_back():
-    """N = 256 output rows up to R = 9 (f16), 128 above; the f16x3 form (hi and
-    lo operands) at N = 128 up to R = 6, 64 up to R = 10, none beyond; the
-    plan reports the wide geometry exactly when a tile fits."""
+def test_wide_tiles_fit():
+    """N = 256 output rows with two operand buffers up to R = 9 (f16), 128
+    above; the hi + lo forms (f16x3, bf16x3) at N = 128 with two buffers up to
+    R = 6 and with one buffer up to R = 12, so every fused radius the
+    tensor-core path takes (t r <= 12) has a wide tile.  The plan reports
+    the wide geometry (128 output columns a tile) for all of them."""
+    order = ((256, 2), (128, 2), (128, 1))
     for R in range(1, 13):
-        nr16 = next((n for n in (256, 128, 64) if geom(R, n, False)[4] <= 227 * 1024), 0)
-        nr3 = next((n for n in (256, 128, 64) if geom(R, n, True)[4] <= 227 * 1024), 0)
-        assert nr16 == (256 if R <= 9 else 128)
-        assert nr3 == (128 if R <= 6 else (64 if R <= 10 else 0))
+        f16 = next((c for c in order if geom(R, c[0], False, c[1])[4] <= 227 * 1024), None)
+        hl = next((c for c in order if geom(R, c[0], True, c[1])[4] <= 227 * 1024), None)
+        assert f16 == ((256, 2) if R <= 9 else (128, 2)), R
+        assert hl == ((128, 2) if R <= 6 else (128, 1)), R
+        # TMEM: two accumulators of N FP32 columns
+        assert 2 * f16[0] <= 512 and 2 * hl[0] <= 512
     w = inputs.weights("box", 2, 1, 3)
-    for t, prec, want_n in ((4, "f16", 128), (11, "f16x3", 16), (12, "f16", 128)):
+    for t, prec in ((4, "f16"), (7, "f16x3"), (11, "f16x3"), (12, "f16"), (12, "bf16x3")):
         p = B.Plan("box", 2, 1, w, "f32", (2048, 2048), t)
         p.set_option("precision", prec)
         p.set_option("path", "tensor_core")
         info = B.stencil_plan_tc_layout(p.handle, t, with_B=False)[0]
         p.close()
-        assert info["n_tile"] == want_n, (t, prec)
+        assert info["n_tile"] == 128, (t, prec)
