@@ -637,7 +637,9 @@ stencil_status launch_dmma2d(const Plan &p, const void *in, void *out, int t, cu
 
 stencil_status launch_tc_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st)
 {
-    if (p.pat.d != 2) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: 2-D grids only");
+    if (p.pat.d == 3 && p.dtype == STENCIL_F32 && p.precision == STENCIL_PREC_F16)
+        return launch_wide3_sweep(p, in, out, t, st);  // t = 1: no band
+    if (p.pat.d != 2) return fail(STENCIL_ERR_UNSUPPORTED, "tensor-core path: 3-D grids in FP32 with precision f16 only");
     stencil_status s;
     if (p.dtype == STENCIL_F64 && p.precision == STENCIL_PREC_OZAKI) {
         return launch_split_sweep(p, in, out, t, st);  // includes the band sweep
@@ -665,12 +667,14 @@ stencil_status read_device_error(int *flag)
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int));
     if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-    int vs = 0, vw = 0;
+    int vs = 0, vw = 0, v3 = 0;
     stencil_status s = read_split_error(&vs);
     if (s != STENCIL_OK) return s;
     s = read_wide_error(&vw);
     if (s != STENCIL_OK) return s;
-    *flag = v | vs | vw;
+    s = read_wide3_error(&v3);
+    if (s != STENCIL_OK) return s;
+    *flag = v | vs | vw | v3;
     return STENCIL_OK;
 }
 

@@ -40,6 +40,14 @@ stencil_status launch_wide_sweep(const Plan &p, const void *in, void *out, int t
 // Read and clear the wide kernel's own error word (part of read_device_error).
 stencil_status read_wide_error(int *flag);
 
+// One sweep (t = 1) of a 3-D FP32 grid on the FP16 tensor cores (k_wide3d.cu,
+// precision f16).  STENCIL_ERR_UNSUPPORTED for t != 1 or when no tile fits
+// (tc_wide3_nrows == 0).
+stencil_status launch_wide3_sweep(const Plan &p, const void *in, void *out, int t, cudaStream_t st);
+
+// Read and clear the 3-D wide kernel's own error word (part of read_device_error).
+stencil_status read_wide3_error(int *flag);
+
 // Read and clear the device error word the tensor-core kernels set when a
 // bounded wait runs out (1 = timed out).
 stencil_status read_device_error(int *flag);

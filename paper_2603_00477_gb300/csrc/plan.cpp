@@ -196,9 +196,9 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
     else g.k_inst = 8;                                         // kind::tf32 K = 8
     if (d == 2 && dtype == STENCIL_F32 && (precision == STENCIL_PREC_TF32 || precision == STENCIL_PREC_TF32X3))
         g.n_tile = tc_ws_ntile(shape, r, t, precision == STENCIL_PREC_TF32X3);
-    if (d == 2 && dtype == STENCIL_F32 &&
+    if (dtype == STENCIL_F32 &&
         (precision == STENCIL_PREC_BF16X3 || precision == STENCIL_PREC_F16 || precision == STENCIL_PREC_F16X3))
-        g.n_tile = 128;  // the wide kernel: 128 output columns per MMA (its M)
+        g.n_tile = 128;  // the wide kernels: 128 output columns per MMA (their M)
     if (d == 2 && path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
         // mma.sp m16n8k16: 16 output columns per block, logical K 16
         SpLayout L = sp_layout_2d(shape, r, t);
@@ -216,20 +216,25 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
         g.available = t * r <= (precision == STENCIL_PREC_OZAKI ? 8 : 12);
         return g;
     }
-    // 3-D (model only): every (plane, row) line of the composite issues its
-    // padded window
+    // 3-D: every (plane, row) line of the composite issues the K blocks of
+    // its window that hold a non-zero column (R - h .. R + h + N - 1 of the
+    // N + 2R columns), as tc_lines_2d counts them; the kernel exists for
+    // FP32 grids in the FP16 form at t = 1 (tc3d_wide)
     std::vector<int> half;
     composite_lines(shape, d, r, t, &half);
+    const int R = t * r;
+    const int kext = (g.n_tile + 2 * R + g.k_inst - 1) / g.k_inst * g.k_inst, nkb = kext / g.k_inst;
     double useful = 0, issued = 0;
-    int kmax = 0;
     for (int h : half) {
-        int kext = (g.n_tile + 2 * h + g.k_inst - 1) / g.k_inst * g.k_inst;
+        if (h < 0) continue;
+        const int lo = (R - h) / g.k_inst, hi = std::min(nkb - 1, (R + h + g.n_tile - 1) / g.k_inst);
         useful += 2 * h + 1;
-        issued += kext;
-        kmax = std::max(kmax, kext);
+        issued += (double)(hi - lo + 1) * g.k_inst;
     }
-    g.kext = kmax;
+    g.kext = kext;
     g.sparsity = issued > 0 ? useful / issued : 0;
+    g.available = d == 3 && dtype == STENCIL_F32 && precision == STENCIL_PREC_F16 &&
+                  path == STENCIL_PATH_TENSOR_CORE && t == 1 && tc_wide3_nrows(shape, r) > 0;
     return g;
 }
 
@@ -237,6 +242,9 @@ TcGeometry tc_geometry(int shape, int d, int r, int t, stencil_dtype dtype, int 
 // FP64 grids on the FP64 MMA, FP32 grids in the TF32 / TF32X3 / BF16X3 forms.
 bool tc_supported(const Plan &p, int precision, int path)
 {
+    if (p.pat.d == 3)  // tc3d_wide: FP32 grids, FP16 form, one step per sweep
+        return path == STENCIL_PATH_TENSOR_CORE && p.dtype == STENCIL_F32 && precision == STENCIL_PREC_F16 &&
+               tc_wide3_nrows(p.pat.shape, p.pat.r) > 0;
     if (p.pat.d != 2) return false;
     if (path == STENCIL_PATH_SPARSE_TENSOR_CORE)  // mma.sp TF32 (1:2 per pair of K)
         return p.dtype == STENCIL_F32 && precision == STENCIL_PREC_TF32;
@@ -289,6 +297,7 @@ constexpr double kWorkerTf32 = 1.30;       // tc2d_ws TF32: in-place rounding, s
 constexpr double kWorkerTf32x3 = 1.65;     // tc2d_ws TF32x3: + the lo split
 constexpr double kWorkerWide = 0.45;       // tc2d_wide, one product: loads, conversion, epilogue (added to the MMAs)
 constexpr double kWorkerWideSplit = 0.28;  // tc2d_wide, three products (128-row tiles, one or two buffers)
+constexpr double kWorkerWide3 = 0.78;      // tc3d_wide, 128-row tiles: plane staging, strips, epilogue, runs
 constexpr double kWorkerSplit = 4.06;      // tc2d_split: FP64 load, exponent, digit cut, recombination
 // sptc2d_sweep issues warp-level mma.sp between its staging and epilogue
 // work, so the two add: 0.92 cycles per output plus 3.15 per sparse
@@ -310,9 +319,27 @@ static double tc_instr_gstencils(const Plan &p, int prec, int path, int t)
 {
     const stencil_peaks pk = peaks();
     const double sm_clk = pk.cu_f32_flops / 256.0;  // SMs x clock (128 FP32 FMA lanes per SM)
-    if (p.pat.d != 2 || sm_clk <= 0) return 0;
+    if (sm_clk <= 0) return 0;
     const int shape = p.pat.shape, r = p.pat.r;
     double per_out = 0;
+    if (p.pat.d == 3) {
+        // tc3d_wide: per output plane tile of 128 columns x nr rows, one MMA
+        // per (line, K block), plus the staging, strips and epilogue
+        const int nr = tc_wide3_nrows(shape, r);
+        if (p.dtype != STENCIL_F32 || prec != STENCIL_PREC_F16 || t != 1 || nr == 0) return 0;
+        std::vector<int> half;
+        composite_lines(shape, 3, r, 1, &half);
+        const int nkb = (128 + 2 * r + 15) / 16;
+        double blocks = 0;
+        for (int h : half)
+            if (h >= 0) blocks += std::min(nkb - 1, (r + h + 127) / 16) - (r - h) / 16 + 1;
+        const double mma = blocks / (128.0 * nr) * std::max(kMmaCycles, 128.0 * nr * 16 / 4096.0);
+        // the per-plane work of a tile (staging its nr + 2r rows, the strips,
+        // the exchanges) is spread over nr rows of outputs
+        per_out = mma + kWorkerWide3 * 128.0 / nr;
+        return sm_clk / per_out / 1e9;
+    }
+    if (p.pat.d != 2) return 0;
     if (path == STENCIL_PATH_SPARSE_TENSOR_CORE) {
         const SpLayout L = sp_layout_2d(shape, r, t);
         double instr = 0;
@@ -443,6 +470,7 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
             int t_hi = p->req_t ? p->req_t : max_fused_t(*p, path);
             for (int t = t_lo; t <= t_hi; t++) {
                 if (path != STENCIL_PATH_CUDA_CORE && t * r > 12) continue;
+                if (path != STENCIL_PATH_CUDA_CORE && d == 3 && t != 1) continue;  // tc3d_wide: t = 1
                 int slices = 0;
                 if (prec == STENCIL_PREC_OZAKI) {
                     if (path != STENCIL_PATH_TENSOR_CORE) continue;
@@ -466,7 +494,10 @@ static stencil_status enumerate(Plan *p, std::vector<Cand> *out)
                         c.tile[1] = 128;
                         c.tile[2] = 16 * split_nacc(t * r, slices);
                     }
-                    if (prec == STENCIL_PREC_BF16X3 || prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
+                    if (d == 3) {
+                        c.tile[1] = tc_wide3_nrows(shape, r);  // one plane: rows (MMA N) x 128 columns
+                        c.tile[2] = 128;
+                    } else if (prec == STENCIL_PREC_BF16X3 || prec == STENCIL_PREC_F16 || prec == STENCIL_PREC_F16X3) {
                         // the wide kernel: output rows (MMA N) x 128 columns
                         const int nr = tc_wide_nrows(r, t, prec != STENCIL_PREC_F16);
                         if (nr == 0) continue;  // t r > 12

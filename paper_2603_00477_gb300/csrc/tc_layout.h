@@ -139,6 +139,43 @@ inline WideTile tc_wide_tile(int r, int t, bool split)
 // Output rows per tile (MMA N) of the wide kernel, 0 if no tile fits.
 inline int tc_wide_nrows(int r, int t, bool split) { return tc_wide_tile(r, t, split).nr; }
 
+// 3-D wide FP16 kernel (tc3d_wide, one step per sweep): the Toeplitz factor
+// of line (dz, dy) is the A operand as in tc2d_wide (one strip per line, two
+// strip sets: the weights are rescaled per output plane), the input is
+// staged one plane tile of nr + 2R rows at a time into a ring of 2R + 2
+// slots.  Lines: the (dz, dy) pairs with a non-zero weight, (2r+1)^2 for a
+// box and 4r + 1 for a star.
+struct Wide3Geom {
+    int nkb, delta, hs, slots;
+    size_t strip_bytes, in_bytes, smem;
+};
+
+inline int tc_wide3_lines(int shape, int r) { return shape == 0 ? (2 * r + 1) * (2 * r + 1) : 4 * r + 1; }  // 0: box
+
+inline Wide3Geom tc_wide3_geom(int R, int nlines, int nr)
+{
+    Wide3Geom g;
+    g.nkb = (128 + 2 * R + 15) / 16;
+    g.delta = std::max(2 * g.nkb, (127 + 2 * R) / 8 + 1);
+    g.hs = (nr + 2 * R) | 1;
+    g.slots = 2 * R + 2;
+    g.strip_bytes = (size_t)((nlines - 1) * g.delta + 2 * g.nkb + 15) * 128;
+    g.in_bytes = (size_t)(2 * g.nkb) * g.hs * 16;
+    // 1 KB header, two strip sets, the ring of input slots
+    g.smem = 1024 + 2 * g.strip_bytes + (size_t)g.slots * g.in_bytes;
+    return g;
+}
+
+// Output rows per tile of the 3-D kernel: the first of 128, 64, 32 whose
+// operands fit in 227 KB; 0 if none does or r > 3.
+inline int tc_wide3_nrows(int shape, int r)
+{
+    if (r < 1 || r > 3) return 0;
+    for (int nr : {128, 64, 32})
+        if (tc_wide3_geom(r, tc_wide3_lines(shape, r), nr).smem <= 227 * 1024) return nr;
+    return 0;
+}
+
 // ---------------------------------------------------------------------------
 // 2:4-structured sparse form (paper Sec. 4.3), TF32 1:2 on mma.sp m16n8k16.
 //

@@ -132,3 +132,47 @@ def test_wide_tiles_fit():
         info = B.stencil_plan_tc_layout(p.handle, t, with_B=False)[0]
         p.close()
         assert info["n_tile"] == 128, (t, prec)
+
+
+def geom3(R, nlines, nr):
+    nkb = (128 + 2 * R + 15) // 16
+    delta = max(2 * nkb, (127 + 2 * R) // 8 + 1)
+    hs = (nr + 2 * R) | 1
+    strip_bytes = ((nlines - 1) * delta + 2 * nkb + 15) * 128
+    return 1024 + 2 * strip_bytes + (2 * R + 2) * 2 * nkb * hs * 16
+
+
+@pytest.mark.parametrize("shape,r,want_nr", [("box", 1, 128), ("star", 1, 128), ("star", 2, 64), ("box", 2, 32),
+                                             ("star", 3, 64)])
+def test_wide3_tiles_and_sparsity(shape, r, want_nr):
+    """The 3-D FP16 kernel: two strip sets of the (dz, dy) lines and a ring of
+    2r + 2 plane tiles in 227 KB decide the rows per tile; the plan reports
+    that tile and S = useful / issued MACs, each line issuing the K blocks of
+    its 128 + 2r window that hold a non-zero column."""
+    lines = [r] * (2 * r + 1) ** 2 if shape == "box" else [r] + [0] * (4 * r)
+    nr = next(n for n in (128, 64, 32) if geom3(r, len(lines), n) <= 227 * 1024)
+    assert nr == want_nr
+    nkb = -(-(128 + 2 * r) // 16)
+    issued = sum((min(nkb - 1, (r + h + 127) // 16) - (r - h) // 16 + 1) * 16 for h in lines)
+    useful = sum(2 * h + 1 for h in lines)
+    w = inputs.weights(shape, 3, r, 1)
+    p = B.Plan(shape, 3, r, w, "f32", (64, 64, 64), 1)
+    p.set_option("precision", "f16")
+    p.set_option("path", "tensor_core")
+    info = p.info()
+    p.close()
+    assert info["tile"] == [1, nr, 128]
+    assert info["sparsity"] == pytest.approx(useful / issued, rel=1e-12)
+
+
+def test_wide3_only_fp16_one_step():
+    """3-D grids take the tensor cores only as FP32 in the FP16 form at t = 1."""
+    w = inputs.weights("box", 3, 1, 1)
+    for dtype, prec, t in (("f64", None, 1), ("f32", "tf32", 1), ("f32", "f16", 2)):
+        p = B.Plan("box", 3, 1, w, dtype, (32, 32, 32), t)
+        with pytest.raises(B.StencilError):
+            if prec:
+                p.set_option("precision", prec)
+            p.set_option("path", "tensor_core")
+            p.info()
+        p.close()
