@@ -241,6 +241,8 @@ def kernel_name(info: dict, d: int, dtype: str, shape: str = "box", r: int = 1) 
         return "cu3d_rot" if rot else "cu3d_stream"
     if info["path"] == 3:
         return "sptc2d_sweep"
+    if d == 3:
+        return "tc3d_wide"
     if dtype == "f64":
         return "tc2d_split" if info["precision_name"] == "ozaki" else "dmma2d_sweep"
     if info["precision_name"] in ("f16", "f16x3", "bf16x3"):

@@ -142,7 +142,7 @@ def test_cli_prints_one_json_line():
 def test_kernel_names():
     """The bench names the sweep kernel a plan launches by the launchers' rules:
     3-D t = 1 FP32 star r <= 3 / box r = 1 on the rotating kernel, the FP16 /
-    BF16 forms on the wide kernel."""
+    BF16 forms on the wide kernel, 3-D FP16 on its z-marching form."""
     bench = importlib.import_module("bench")
     kn = bench.kernel_name
     assert kn({"path": 1, "t": 1, "precision_name": "native"}, 2, "f64") == "cu2d_sweep"
@@ -158,3 +158,4 @@ def test_kernel_names():
     assert kn({"path": 2, "t": 4, "precision_name": "f16", "tile": [1, 256, 128]}, 2, "f32") == "tc2d_wide"
     assert kn({"path": 2, "t": 6, "precision_name": "f16x3", "tile": [1, 128, 128]}, 2, "f32") == "tc2d_wide"
     assert kn({"path": 3, "t": 3, "precision_name": "tf32"}, 2, "f32") == "sptc2d_sweep"
+    assert kn({"path": 2, "t": 1, "precision_name": "f16", "tile": [1, 128, 128]}, 3, "f32", "box", 1) == "tc3d_wide"
