@@ -591,9 +591,10 @@ def table3_leg(B, inputs, stream):
     with the model's prediction and scenario for both, the measured
     direction of change (tensor-core rate / CUDA-core rate) next to the
     paper's A100 one, and this engine's fastest tensor-core form for the
-    case (FP64 by exact splitting; FP16 with the operands exchanged).  This
-    engine has no 3-D tensor-core tiles: 3-D cases run on CUDA cores (at the
-    case's t and at t = 1)."""
+    case (FP64 by exact splitting; FP16 with the operands exchanged).  The
+    3-D cases are fused (t = 3, 7), which the 3-D tensor-core kernel (t = 1)
+    does not cover: they run on CUDA cores at the case's t and at t = 1, and
+    the FP32 case also in the 3-D FP16 tensor-core form at t = 1."""
     import numpy as np
     import torch
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_table3.json")))
@@ -612,8 +613,11 @@ def table3_leg(B, inputs, stream):
         if d == 2:
             forms.append(("sparse_tensor_core", "tf32", t) if case["tc"] == "sptc_tf32" else ("tensor_core", "native", t))
             forms.append(("tensor_core", "ozaki" if D == 8 else "f16", t))
-        elif t != 1:
-            forms.append(("cuda_core", None, 1))
+        else:
+            if t != 1:
+                forms.append(("cuda_core", None, 1))
+            if D == 4:
+                forms.append(("tensor_core", "f16", 1))
         res = {"case": case["case"], "stencil": f"{shape.capitalize()}-{d}D{r}R", "t": t, "dtype": dtype,
                "dims": list(dims), "steps_per_run": steps, "paper_change_a100": case["change"], "forms": []}
         for path, prec, tt in forms:
