@@ -92,8 +92,10 @@ typedef enum {
  * a power-of-two scale per staged tile (and one for the composite weights),
  * one product (F16: 11 significant bits, TF32's) or hi + lo parts with three
  * products (F16X3: 22 bits, TF32x3's), FP32 accumulation; a kind::f16 MMA
- * takes K = 16 per instruction against TF32's 8.  ANY: the dispatcher may
- * pick any form the grid type allows. */
+ * takes K = 16 per instruction against TF32's 8.  3-D grids take the
+ * tensor-core path only as FP32 in the F16 form at t = 1 (box r <= 2, star
+ * r <= 3; a power-of-two scale per staged plane tile).  ANY: the dispatcher
+ * may pick any form the grid type allows. */
 typedef enum {
     STENCIL_PREC_NATIVE = 0,
     STENCIL_PREC_TF32 = 1,
